@@ -1,0 +1,606 @@
+/*
+ * lbm_oracle.c -- plain FP64 CPU oracle for the two D2Q9 multiphase time steps
+ * compared in "Fundamental comparison between the pseudopotential and the free
+ * energy lattice Boltzmann methods" (Czelusniak et al., arXiv:2403.11167).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
+ * calls this file; only the test-suite, the smoke check and the CPU-baseline leg
+ * of the benchmark load it.  It shares no code, header, table or constant
+ * generator with the CUDA path.
+ *
+ * What it computes, in the paper's order and notation (lattice units,
+ * dx = dt = c = 1, c_s^2 = 1/3, G = -1):
+ *
+ *   Eq. (1)  MRT lattice Boltzmann equation
+ *              f_i(x + c_i, t+1) = f_i - [M^-1 L M](f - f^eq)
+ *                                      + [M^-1 (I - L/2) M] F' + C_i
+ *            with the moment matrix M of Eq. (S48), M^-1 obtained by a plain
+ *            Gauss-Jordan inversion of M (checked against the printed Eq. (S49)
+ *            by the tests) and L = diag of Eq. (3).
+ *   Modified pseudopotential model (MP-LBM, Sec. 4):
+ *            Eq. (28) EOS, Eq. (11) psi, Eq. (10) Shan-Chen force,
+ *            Eqs. (30a/b, 31a/b) Q tensor, Eq. (13) source MC,
+ *            Eq. (32) forcing moments MF', Eq. (4) equilibrium, Eq. (6) macros.
+ *            Reading of Eq. (30b): the C2 term carries the factor G like the
+ *            C1 and kappa^Li terms, as the continuum form Eq. (S41b) requires.
+ *   Improved well-balanced free-energy model (IWB-FE-LBM, Sec. 2.2):
+ *            Eq. (29) bulk chemical potential, Eq. (24) 9-point stencils
+ *            (gradient stencil read with the weights w_i), mu = mu_b - kappa lap rho,
+ *            F = -rho grad mu, Eq. (20) equilibrium (A = 0, p_g = 0),
+ *            Eq. (21) forcing with d = 2 and grad p_g = 0.
+ *
+ * Everything is done cell by cell with explicit 9x9 matrix products; no fusion,
+ * no reordering beyond the equations.  Fields are SoA: f[i*ny*nx + y*nx + x],
+ * periodic in both directions.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q9 9
+
+/* Eq. (2): D2Q9 velocities, i = 0 rest, 1..4 axes, 5..8 diagonals. */
+static const int CX[Q9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[Q9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+/* Weights below Eq. (4). */
+static const double WI[Q9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2 = 1.0 / 3.0;
+
+/* Eq. (S48): Lallemand-Luo moment matrix; rows rho, e, zeta, jx, qx, jy, qy, pxx, pxy. */
+static const double MM[Q9][Q9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},     {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1}, {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},  {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},  {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+typedef struct {
+    double a, b, R, T;  /* Carnahan-Starling EOS, Eq. (28) */
+    double G;           /* interaction strength, -1 (text below Eq. 11) */
+    double tau_rho, tau_e, tau_zeta, tau_j, tau_q, tau_nu; /* Eq. (3) */
+    double kappa_P, kappa_Li, sigma_Li; /* MP-LBM, Eqs. (30)-(32) */
+    double kappa;       /* FE-LBM surface-tension parameter, mu = mu_b - kappa lap rho */
+    double fx, fy;      /* constant body force added to the total force */
+} orc_params;
+
+/* ------------------------------------------------------------------------ */
+/* M^-1 by Gauss-Jordan elimination with partial pivoting.                  */
+static void invert9(const double A[Q9][Q9], double Ainv[Q9][Q9]) {
+    double a[Q9][2 * Q9];
+    for (int r = 0; r < Q9; ++r)
+        for (int c = 0; c < 2 * Q9; ++c)
+            a[r][c] = c < Q9 ? A[r][c] : (c - Q9 == r ? 1.0 : 0.0);
+    for (int col = 0; col < Q9; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < Q9; ++r)
+            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        if (piv != col)
+            for (int c = 0; c < 2 * Q9; ++c) {
+                double t = a[col][c];
+                a[col][c] = a[piv][c];
+                a[piv][c] = t;
+            }
+        double d = a[col][col];
+        for (int c = 0; c < 2 * Q9; ++c) a[col][c] /= d;
+        for (int r = 0; r < Q9; ++r) {
+            if (r == col) continue;
+            double m = a[r][col];
+            if (m != 0.0)
+                for (int c = 0; c < 2 * Q9; ++c) a[r][c] -= m * a[col][c];
+        }
+    }
+    for (int r = 0; r < Q9; ++r)
+        for (int c = 0; c < Q9; ++c) Ainv[r][c] = a[r][Q9 + c];
+}
+
+static double MINV[Q9][Q9];
+static int minv_ready = 0;
+static void ensure_minv(void) {
+    if (!minv_ready) {
+        invert9(MM, MINV);
+        minv_ready = 1;
+    }
+}
+
+void orc_moment_matrix(double* out81) {
+    for (int r = 0; r < Q9; ++r)
+        for (int c = 0; c < Q9; ++c) out81[r * Q9 + c] = MM[r][c];
+}
+void orc_moment_matrix_inverse(double* out81) {
+    ensure_minv();
+    for (int r = 0; r < Q9; ++r)
+        for (int c = 0; c < Q9; ++c) out81[r * Q9 + c] = MINV[r][c];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thermodynamics.                                                          */
+/* Eq. (28): Carnahan-Starling pressure. */
+static double p_eos(const orc_params* p, double rho) {
+    double eta = p->b * rho / 4.0;
+    return rho * p->R * p->T * (1.0 + eta + eta * eta - eta * eta * eta) /
+               ((1.0 - eta) * (1.0 - eta) * (1.0 - eta)) -
+           p->a * rho * rho;
+}
+/* Eq. (29): bulk chemical potential. */
+static double mu_bulk(const orc_params* p, double rho) {
+    double eta = p->b * rho / 4.0;
+    double RT = p->R * p->T;
+    return RT * (3.0 - eta) / ((1.0 - eta) * (1.0 - eta) * (1.0 - eta)) + RT * log(rho) + RT -
+           2.0 * p->a * rho;
+}
+double orc_p_eos(const orc_params* p, double rho) { return p_eos(p, rho); }
+double orc_mu_bulk(const orc_params* p, double rho) { return mu_bulk(p, rho); }
+
+/* Eq. (11): psi = sqrt(2 (p_EOS - rho c_s^2) / (G c^2 dt^2)).  Returns -1 if the
+ * radicand is negative (the pseudopotential does not exist there). */
+static double psi_of(const orc_params* p, double rho) {
+    double rad = 2.0 * (p_eos(p, rho) - rho * CS2) / p->G;
+    if (!(rad >= 0.0)) return -1.0;
+    return sqrt(rad);
+}
+
+static inline int wrap(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Equilibria.                                                               */
+/* Eq. (4): standard second-order equilibrium (used by the pseudopotential model). */
+static void feq_standard(double rho, double ux, double uy, double feq[Q9]) {
+    double uu = ux * ux + uy * uy;
+    for (int i = 0; i < Q9; ++i) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        /* (c_a c_b - c_s^2 d_ab) u_a u_b / (2 c_s^4) */
+        double quad = (cu * cu - CS2 * uu) / (2.0 * CS2 * CS2);
+        feq[i] = WI[i] * rho * (1.0 + cu / CS2 + quad);
+    }
+}
+
+/* Eq. (20) with A = 0 and p_g = 0: improved well-balanced equilibrium. */
+static void feq_wellbalanced(double rho, double ux, double uy, double feq[Q9]) {
+    double uu = ux * ux + uy * uy;
+    feq[0] = rho - WI[0] * rho * uu / (2.0 * CS2);
+    for (int i = 1; i < Q9; ++i) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        feq[i] = WI[i] * rho * (cu / CS2 + (cu * cu - CS2 * uu) / (2.0 * CS2 * CS2));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initialisation: f = f^eq(rho0, u = 0) of the model (model 0 = MP-LBM, 1 = FE). */
+void orc_init(int model, int nx, int ny, const double* rho0, double* f) {
+    size_t N = (size_t)nx * ny;
+    for (size_t c = 0; c < N; ++c) {
+        double feq[Q9];
+        if (model == 0)
+            feq_standard(rho0[c], 0.0, 0.0, feq);
+        else
+            feq_wellbalanced(rho0[c], 0.0, 0.0, feq);
+        for (int i = 0; i < Q9; ++i) f[(size_t)i * N + c] = feq[i];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pseudopotential (MP-LBM) pieces, cell-local given the psi field.          */
+
+/* Eq. (10): Shan-Chen force, omega(1) = 1/3, omega(2) = 1/12. */
+static double omega_of(int i) { return (CX[i] * CX[i] + CY[i] * CY[i]) == 1 ? 1.0 / 3.0 : 1.0 / 12.0; }
+
+static void sc_force(const orc_params* p, const double* psi, int nx, int ny, int x, int y,
+                     double* Fx, double* Fy) {
+    double sx = 0.0, sy = 0.0;
+    for (int i = 1; i < Q9; ++i) {
+        double pn = psi[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)];
+        sx += omega_of(i) * pn * CX[i];
+        sy += omega_of(i) * pn * CY[i];
+    }
+    double pc = psi[y * nx + x];
+    *Fx = -p->G * pc * sx;
+    *Fy = -p->G * pc * sy;
+}
+
+/* Eqs. (30a), (30b), (31a), (31b): width-control tensor Q_ab. */
+static void q_tensor(const orc_params* p, const double* psi, int nx, int ny, int x, int y,
+                     double Q[2][2]) {
+    double C1 = 5.0 / 6.0 * (p->kappa_P - 1.0);
+    double C2 = 0.5 * (1.0 - p->kappa_P);
+    double pc = psi[y * nx + x];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) Q[a][b] = 0.0;
+    for (int i = 1; i < Q9; ++i) {
+        double pn = psi[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)];
+        double c[2] = {(double)CX[i], (double)CY[i]};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                double d = (a == b) ? 1.0 : 0.0;
+                double Ciab = C1 * p->G * d + C2 * p->G * (c[a] * c[b] - CS2 * d) +
+                              p->kappa_Li * p->G / 2.0 * c[a] * c[b];
+                Q[a][b] += omega_of(i) * Ciab * (pn - pc);
+            }
+    }
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) Q[a][b] *= pc;
+}
+
+/* Relaxation rates, Eq. (3): L = diag(1/tau_rho, 1/tau_e, 1/tau_zeta, 1/tau_j,
+ * 1/tau_q, 1/tau_j, 1/tau_q, 1/tau_nu, 1/tau_nu). */
+static void lambda_diag(const orc_params* p, double L[Q9]) {
+    L[0] = 1.0 / p->tau_rho;
+    L[1] = 1.0 / p->tau_e;
+    L[2] = 1.0 / p->tau_zeta;
+    L[3] = 1.0 / p->tau_j;
+    L[4] = 1.0 / p->tau_q;
+    L[5] = 1.0 / p->tau_j;
+    L[6] = 1.0 / p->tau_q;
+    L[7] = 1.0 / p->tau_nu;
+    L[8] = 1.0 / p->tau_nu;
+}
+
+/* Density, psi, force and velocity of the pseudopotential model for the whole
+ * lattice (Eqs. 6a, 11, 10, 6b). psi < 0 marks a negative radicand. */
+static int pp_fields(const orc_params* p, int nx, int ny, const double* f, double* rho,
+                     double* psi, double* Fx, double* Fy, double* ux, double* uy) {
+    size_t N = (size_t)nx * ny;
+    int bad = 0;
+    for (size_t c = 0; c < N; ++c) {
+        double s = 0.0;
+        for (int i = 0; i < Q9; ++i) s += f[(size_t)i * N + c];
+        rho[c] = s;
+        psi[c] = psi_of(p, s);
+        if (psi[c] < 0.0 || !(s > 0.0)) bad = 1;
+    }
+    if (bad) return -1;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            double fix, fiy;
+            sc_force(p, psi, nx, ny, x, y, &fix, &fiy);
+            Fx[c] = fix + p->fx;
+            Fy[c] = fiy + p->fy;
+            double jx = 0.0, jy = 0.0;
+            for (int i = 0; i < Q9; ++i) {
+                jx += f[(size_t)i * N + c] * CX[i];
+                jy += f[(size_t)i * N + c] * CY[i];
+            }
+            ux[c] = (jx + Fx[c] / 2.0) / rho[c];
+            uy[c] = (jy + Fy[c] / 2.0) / rho[c];
+        }
+    return 0;
+}
+
+/* One MP-LBM time step: collision per Eq. (1) with Eqs. (4), (13), (30)-(32), then
+ * streaming f_i(x + c_i) <- f*_i(x).  f is read, fnew written.  Returns 0 or -1
+ * if rho <= 0 or the psi radicand is negative somewhere. */
+static int pp_step(const orc_params* p, int nx, int ny, const double* f, double* fnew,
+                   double* rho, double* psi, double* Fx, double* Fy, double* ux, double* uy) {
+    size_t N = (size_t)nx * ny;
+    if (pp_fields(p, nx, ny, f, rho, psi, Fx, Fy, ux, uy)) return -1;
+    double L[Q9];
+    lambda_diag(p, L);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            double fc[Q9], feq[Q9], m[Q9], meq[Q9], MF[Q9], MC[Q9], dm[Q9];
+            for (int i = 0; i < Q9; ++i) fc[i] = f[(size_t)i * N + c];
+            feq_standard(rho[c], ux[c], uy[c], feq);
+            for (int k = 0; k < Q9; ++k) {
+                m[k] = 0.0;
+                meq[k] = 0.0;
+                for (int j = 0; j < Q9; ++j) {
+                    m[k] += MM[k][j] * fc[j];
+                    meq[k] += MM[k][j] * feq[j];
+                }
+            }
+            /* Eq. (32): forcing in moment space.  The consistency term uses only the
+             * interaction force F_int; the velocity terms use the total force. */
+            double fix = Fx[c] - p->fx, fiy = Fy[c] - p->fy;
+            double Fint2 = fix * fix + fiy * fiy;
+            double uF = ux[c] * Fx[c] + uy[c] * Fy[c];
+            double ps2 = psi[c] * psi[c];
+            MF[0] = 0.0;
+            MF[1] = 6.0 * uF + 12.0 * p->kappa_P * p->sigma_Li * Fint2 / (ps2 * (p->tau_e - 0.5));
+            MF[2] = -6.0 * uF - 12.0 * p->kappa_P * p->sigma_Li * Fint2 / (ps2 * (p->tau_zeta - 0.5));
+            MF[3] = Fx[c];
+            MF[4] = -Fx[c];
+            MF[5] = Fy[c];
+            MF[6] = -Fy[c];
+            MF[7] = 2.0 * (ux[c] * Fx[c] - uy[c] * Fy[c]);
+            MF[8] = ux[c] * Fy[c] + uy[c] * Fx[c];
+            /* Eq. (13) with the modified Q of Eq. (30). */
+            double Q[2][2];
+            q_tensor(p, psi, nx, ny, x, y, Q);
+            MC[0] = 0.0;
+            MC[1] = 1.5 / p->tau_e * (Q[0][0] + Q[1][1]);
+            MC[2] = -1.5 / p->tau_zeta * (Q[0][0] + Q[1][1]);
+            MC[3] = MC[4] = MC[5] = MC[6] = 0.0;
+            MC[7] = -1.0 / p->tau_nu * (Q[0][0] - Q[1][1]);
+            MC[8] = -1.0 / p->tau_nu * Q[0][1];
+            /* Eq. (1): f* = f - M^-1 L (m - m^eq) + M^-1 (I - L/2) MF' + M^-1 MC. */
+            for (int k = 0; k < Q9; ++k)
+                dm[k] = -L[k] * (m[k] - meq[k]) + (1.0 - L[k] / 2.0) * MF[k] + MC[k];
+            for (int i = 0; i < Q9; ++i) {
+                double s = 0.0;
+                for (int k = 0; k < Q9; ++k) s += MINV[i][k] * dm[k];
+                int xd = wrap(x + CX[i], nx), yd = wrap(y + CY[i], ny);
+                fnew[(size_t)i * N + (size_t)yd * nx + xd] = fc[i] + s;
+            }
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Free-energy (IWB-FE-LBM) pieces.                                          */
+
+/* Eq. (24): grad phi = (1/c_s^2) sum_i w_i phi(x + c_i) c_i;
+ *           lap phi  = (2/c_s^2) sum_i w_i [phi(x + c_i) - phi(x)]. */
+static void stencil_grad(const double* phi, int nx, int ny, int x, int y, double* gx, double* gy) {
+    double sx = 0.0, sy = 0.0;
+    for (int i = 0; i < Q9; ++i) {
+        double v = phi[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)];
+        sx += WI[i] * v * CX[i];
+        sy += WI[i] * v * CY[i];
+    }
+    *gx = sx / CS2;
+    *gy = sy / CS2;
+}
+static double stencil_lap(const double* phi, int nx, int ny, int x, int y) {
+    double s = 0.0, pc = phi[y * nx + x];
+    for (int i = 0; i < Q9; ++i) s += WI[i] * (phi[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)] - pc);
+    return 2.0 / CS2 * s;
+}
+
+/* Density, chemical potential, gradients, force and velocity of the FE model. */
+static int fe_fields(const orc_params* p, int nx, int ny, const double* f, double* rho,
+                     double* mu, double* Fx, double* Fy, double* ux, double* uy, double* drx,
+                     double* dry) {
+    size_t N = (size_t)nx * ny;
+    for (size_t c = 0; c < N; ++c) {
+        double s = 0.0;
+        for (int i = 0; i < Q9; ++i) s += f[(size_t)i * N + c];
+        rho[c] = s;
+        if (!(s > 0.0) || !(p->b * s / 4.0 < 1.0)) return -1;
+    }
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            mu[c] = mu_bulk(p, rho[c]) - p->kappa * stencil_lap(rho, nx, ny, x, y);
+        }
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            double gmx, gmy;
+            stencil_grad(mu, nx, ny, x, y, &gmx, &gmy);
+            stencil_grad(rho, nx, ny, x, y, &drx[c], &dry[c]);
+            Fx[c] = -rho[c] * gmx + p->fx;
+            Fy[c] = -rho[c] * gmy + p->fy;
+            double jx = 0.0, jy = 0.0;
+            for (int i = 0; i < Q9; ++i) {
+                jx += f[(size_t)i * N + c] * CX[i];
+                jy += f[(size_t)i * N + c] * CY[i];
+            }
+            ux[c] = (jx + Fx[c] / 2.0) / rho[c];
+            uy[c] = (jy + Fy[c] / 2.0) / rho[c];
+        }
+    return 0;
+}
+
+/* One IWB-FE-LBM step: Eq. (1) with Eq. (20) equilibrium, Eq. (21) forcing, C_i = 0. */
+static int fe_step(const orc_params* p, int nx, int ny, const double* f, double* fnew,
+                   double* rho, double* mu, double* Fx, double* Fy, double* ux, double* uy,
+                   double* drx, double* dry) {
+    size_t N = (size_t)nx * ny;
+    if (fe_fields(p, nx, ny, f, rho, mu, Fx, Fy, ux, uy, drx, dry)) return -1;
+    double L[Q9];
+    lambda_diag(p, L);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            double fc[Q9], feq[Q9], Fi[Q9], m[Q9], meq[Q9], MF[Q9], dm[Q9];
+            for (int i = 0; i < Q9; ++i) fc[i] = f[(size_t)i * N + c];
+            feq_wellbalanced(rho[c], ux[c], uy[c], feq);
+            /* Eq. (21), d = 2, grad p_g = 0:
+             * F_i = w_i [ c_a F_a / c_s^2
+             *           + (c_a c_b - c_s^2 d_ab) u_a (F_b + c_s^2 d_b rho) / c_s^4
+             *           + 1/2 (|c|^2 / c_s^2 - d) u_g d_g rho ] */
+            double u[2] = {ux[c], uy[c]}, F[2] = {Fx[c], Fy[c]}, gr[2] = {drx[c], dry[c]};
+            double ugr = u[0] * gr[0] + u[1] * gr[1];
+            for (int i = 0; i < Q9; ++i) {
+                double ci[2] = {(double)CX[i], (double)CY[i]};
+                double t1 = (ci[0] * F[0] + ci[1] * F[1]) / CS2;
+                double t2 = 0.0;
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b) {
+                        double d = (a == b) ? 1.0 : 0.0;
+                        t2 += (ci[a] * ci[b] - CS2 * d) * u[a] * (F[b] + CS2 * gr[b]);
+                    }
+                t2 /= CS2 * CS2;
+                double c2 = ci[0] * ci[0] + ci[1] * ci[1];
+                double t3 = 0.5 * (c2 / CS2 - 2.0) * ugr;
+                Fi[i] = WI[i] * (t1 + t2 + t3);
+            }
+            for (int k = 0; k < Q9; ++k) {
+                m[k] = meq[k] = MF[k] = 0.0;
+                for (int j = 0; j < Q9; ++j) {
+                    m[k] += MM[k][j] * fc[j];
+                    meq[k] += MM[k][j] * feq[j];
+                    MF[k] += MM[k][j] * Fi[j];
+                }
+            }
+            for (int k = 0; k < Q9; ++k) dm[k] = -L[k] * (m[k] - meq[k]) + (1.0 - L[k] / 2.0) * MF[k];
+            for (int i = 0; i < Q9; ++i) {
+                double s = 0.0;
+                for (int k = 0; k < Q9; ++k) s += MINV[i][k] * dm[k];
+                int xd = wrap(x + CX[i], nx), yd = wrap(y + CY[i], ny);
+                fnew[(size_t)i * N + (size_t)yd * nx + xd] = fc[i] + s;
+            }
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public entry points (ctypes).                                            */
+
+typedef struct {
+    double *rho, *aux, *Fx, *Fy, *ux, *uy, *drx, *dry, *ftmp;
+} work_t;
+
+static int work_alloc(work_t* w, size_t N) {
+    memset(w, 0, sizeof(*w));
+    w->rho = malloc(N * sizeof(double));
+    w->aux = malloc(N * sizeof(double));
+    w->Fx = malloc(N * sizeof(double));
+    w->Fy = malloc(N * sizeof(double));
+    w->ux = malloc(N * sizeof(double));
+    w->uy = malloc(N * sizeof(double));
+    w->drx = malloc(N * sizeof(double));
+    w->dry = malloc(N * sizeof(double));
+    w->ftmp = malloc(Q9 * N * sizeof(double));
+    return (w->rho && w->aux && w->Fx && w->Fy && w->ux && w->uy && w->drx && w->dry && w->ftmp) ? 0 : -1;
+}
+static void work_free(work_t* w) {
+    free(w->rho); free(w->aux); free(w->Fx); free(w->Fy); free(w->ux);
+    free(w->uy); free(w->drx); free(w->dry); free(w->ftmp);
+}
+
+/* Advance f (in place, SoA [9][ny][nx]) by nsteps time steps of the given model.
+ * nthreads <= 0 keeps the OpenMP default.  Returns the number of steps done
+ * (< nsteps if the state became invalid: rho <= 0, eta >= 1 or psi^2 < 0). */
+long orc_run(int model, const orc_params* p, int nx, int ny, double* f, long nsteps, int nthreads) {
+    ensure_minv();
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    size_t N = (size_t)nx * ny;
+    work_t w;
+    if (work_alloc(&w, N)) {
+        work_free(&w);
+        return -1;
+    }
+    double *cur = f, *nxt = w.ftmp;
+    long s;
+    for (s = 0; s < nsteps; ++s) {
+        int rc = model == 0 ? pp_step(p, nx, ny, cur, nxt, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy)
+                            : fe_step(p, nx, ny, cur, nxt, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy,
+                                      w.drx, w.dry);
+        if (rc) break;
+        double* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (cur != f) memcpy(f, cur, Q9 * N * sizeof(double));
+    work_free(&w);
+    return s;
+}
+
+/* Macroscopic fields of the current populations: rho (Eq. 6a), u including the
+ * half-force shift (Eq. 6b), the total force, and the model's auxiliary field
+ * (psi for the pseudopotential model, mu for the free-energy model). */
+int orc_macro(int model, const orc_params* p, int nx, int ny, const double* f, double* rho,
+              double* ux, double* uy, double* Fx, double* Fy, double* aux) {
+    size_t N = (size_t)nx * ny;
+    work_t w;
+    if (work_alloc(&w, N)) {
+        work_free(&w);
+        return -1;
+    }
+    int rc = model == 0 ? pp_fields(p, nx, ny, f, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy)
+                        : fe_fields(p, nx, ny, f, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy, w.drx, w.dry);
+    if (rc == 0) {
+        if (rho) memcpy(rho, w.rho, N * sizeof(double));
+        if (ux) memcpy(ux, w.ux, N * sizeof(double));
+        if (uy) memcpy(uy, w.uy, N * sizeof(double));
+        if (Fx) memcpy(Fx, w.Fx, N * sizeof(double));
+        if (Fy) memcpy(Fy, w.Fy, N * sizeof(double));
+        if (aux) memcpy(aux, w.aux, N * sizeof(double));
+    }
+    work_free(&w);
+    return rc;
+}
+
+/* Cell-local building blocks exposed for the moment tests (Eqs. 4, 20, 21, 32, 13). */
+void orc_feq(int model, double rho, double ux, double uy, double* feq) {
+    if (model == 0)
+        feq_standard(rho, ux, uy, feq);
+    else
+        feq_wellbalanced(rho, ux, uy, feq);
+}
+
+/* Population-space forcing of the FE model, Eq. (21), for given u, F, grad rho. */
+void orc_fe_forcing(double ux, double uy, double Fx, double Fy, double gx, double gy, double* Fi) {
+    double u[2] = {ux, uy}, F[2] = {Fx, Fy}, gr[2] = {gx, gy};
+    double ugr = ux * gx + uy * gy;
+    for (int i = 0; i < Q9; ++i) {
+        double ci[2] = {(double)CX[i], (double)CY[i]};
+        double t1 = (ci[0] * F[0] + ci[1] * F[1]) / CS2, t2 = 0.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                t2 += (ci[a] * ci[b] - CS2 * (a == b)) * u[a] * (F[b] + CS2 * gr[b]);
+        t2 /= CS2 * CS2;
+        double c2 = ci[0] * ci[0] + ci[1] * ci[1];
+        Fi[i] = WI[i] * (t1 + t2 + 0.5 * (c2 / CS2 - 2.0) * ugr);
+    }
+}
+
+/* Population-space pieces S_i = [M^-1 (I - L/2) M] F' and C_i = M^-1 MC of the
+ * pseudopotential model at one cell, for given u, F, F_int, psi and Q (Eqs. 32, 13). */
+void orc_pp_sources(const orc_params* p, double ux, double uy, double Fx, double Fy,
+                    double Fix, double Fiy, double psi, double Qxx, double Qyy, double Qxy,
+                    double* S, double* C) {
+    ensure_minv();
+    double L[Q9], MF[Q9], MC[Q9];
+    lambda_diag(p, L);
+    double uF = ux * Fx + uy * Fy, Fint2 = Fix * Fix + Fiy * Fiy, ps2 = psi * psi;
+    MF[0] = 0.0;
+    MF[1] = 6.0 * uF + 12.0 * p->kappa_P * p->sigma_Li * Fint2 / (ps2 * (p->tau_e - 0.5));
+    MF[2] = -6.0 * uF - 12.0 * p->kappa_P * p->sigma_Li * Fint2 / (ps2 * (p->tau_zeta - 0.5));
+    MF[3] = Fx; MF[4] = -Fx; MF[5] = Fy; MF[6] = -Fy;
+    MF[7] = 2.0 * (ux * Fx - uy * Fy);
+    MF[8] = ux * Fy + uy * Fx;
+    MC[0] = 0.0;
+    MC[1] = 1.5 / p->tau_e * (Qxx + Qyy);
+    MC[2] = -1.5 / p->tau_zeta * (Qxx + Qyy);
+    MC[3] = MC[4] = MC[5] = MC[6] = 0.0;
+    MC[7] = -1.0 / p->tau_nu * (Qxx - Qyy);
+    MC[8] = -1.0 / p->tau_nu * Qxy;
+    for (int i = 0; i < Q9; ++i) {
+        double s = 0.0, c = 0.0;
+        for (int k = 0; k < Q9; ++k) {
+            s += MINV[i][k] * (1.0 - L[k] / 2.0) * MF[k];
+            c += MINV[i][k] * MC[k];
+        }
+        S[i] = s;
+        C[i] = c;
+    }
+}
+
+/* Q tensor of Eq. (30) on a given psi field at (x, y): out = {Qxx, Qyy, Qxy}. */
+void orc_q_tensor(const orc_params* p, const double* psi, int nx, int ny, int x, int y, double* out) {
+    double Q[2][2];
+    q_tensor(p, psi, nx, ny, x, y, Q);
+    out[0] = Q[0][0];
+    out[1] = Q[1][1];
+    out[2] = Q[0][1];
+}
+
+/* Stencils of Eq. (24) on a given field at (x, y): out = {d_x, d_y, lap}. */
+void orc_stencils(const double* phi, int nx, int ny, int x, int y, double* out) {
+    stencil_grad(phi, nx, ny, x, y, &out[0], &out[1]);
+    out[2] = stencil_lap(phi, nx, ny, x, y);
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

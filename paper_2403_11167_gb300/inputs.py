@@ -1,0 +1,40 @@
+"""Seeded synthetic initial density fields (the input recipes of the workloads).
+
+This module holds no arithmetic of the lattice Boltzmann method: it only draws
+or shapes initial densities, given the two bulk densities as arguments.  Both
+the CUDA path and the FP64 oracle are fed from here.
+
+Recipes (the paper initialises every run from f = f^eq(rho0, u = 0), Secs. 5.3-5.4):
+
+* ``flat_slab`` -- liquid slab in the middle half of x, vapour elsewhere,
+  rho(x) = rho_v + (rho_l - rho_v)/2 [tanh(2(x - nx/4)/W0) - tanh(2(x - 3nx/4)/W0)].
+* ``droplet`` -- rho = (rho_l + rho_v)/2 - (rho_l - rho_v)/2 tanh(2(r - R)/W0),
+  r measured from ((nx - 1)/2, (ny - 1)/2).
+* ``spinodal_noise`` -- rho = rho_mean (1 + U(-amp, amp)), i.i.d. per cell from
+  NumPy's PCG64 with the given seed (spinodal decomposition from a uniform state).
+* ``random_field`` -- i.i.d. uniform densities in [lo, hi] (brute-force checks).
+"""
+import numpy as np
+
+
+def flat_slab(nx: int, ny: int, rho_v: float, rho_l: float, w0: float = 5.0) -> np.ndarray:
+    x = np.arange(nx, dtype=np.float64)
+    x1, x2 = nx / 4.0, 3.0 * nx / 4.0
+    prof = rho_v + 0.5 * (rho_l - rho_v) * (np.tanh(2.0 * (x - x1) / w0) - np.tanh(2.0 * (x - x2) / w0))
+    return np.ascontiguousarray(np.broadcast_to(prof, (ny, nx)))
+
+
+def droplet(nx: int, ny: int, radius: float, rho_v: float, rho_l: float, w0: float = 5.0) -> np.ndarray:
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    r = np.sqrt((xx - (nx - 1) / 2.0) ** 2 + (yy - (ny - 1) / 2.0) ** 2)
+    return 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * np.tanh(2.0 * (r - radius) / w0)
+
+
+def spinodal_noise(nx: int, ny: int, rho_mean: float, amp: float = 0.01, seed: int = 2403) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rho_mean * (1.0 + rng.uniform(-amp, amp, size=(ny, nx)))
+
+
+def random_field(nx: int, ny: int, lo: float, hi: float, seed: int = 0) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=(ny, nx))
