@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused D2Q9 multiphase time step on GB300.
+
+Workload (one bench "step" = one pass of the whole hot path over one batch): a
+4096 x 4096 periodic D2Q9 lattice, Carnahan-Starling EOS (a = 0.25, b = 4, R = 1)
+at Tr = 0.85, tau = 0.8, spinodal decomposition from rho = (rho_l + rho_v)/2 (1 +
+U(-0.01, 0.01)) (seed 2403), 2000 FP32 time steps of the pseudopotential model and
+2000 of the free-energy model, each started from f = f^eq(rho0).
+
+Prints one JSON line.  ``value`` is MLUPS with the initial density already in HBM;
+``e2e`` is the same metric through the public C ABI with the FP64 initial density
+in pinned host memory, host->device copy, time stepping and observables read-back
+inside the timed region.  ``--impl reference`` times the FP64 CPU oracle instead.
+Multi-GPU (torchrun): independent replicas, one lattice per rank (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 multiphase MLUPS & HBM-roofline fraction; sweep runs/s batched vs plain"
+BYTES_PER_CELL_F32 = 72  # 9 loads + 9 stores of FP32 populations per cell update
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--lbm-steps", type=int, default=2000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(args):
+    return {
+        "workload": f"spinodal decomposition, {args.size}x{args.size} periodic D2Q9, Carnahan-Starling a=0.25 "
+                    f"Tr=0.85, tau=0.8, {args.lbm_steps} steps each of the pseudopotential and free-energy models",
+        "nx": args.size, "ny": args.size, "lbm_steps_per_model": args.lbm_steps,
+        "models": ["pseudopotential (MP-LBM)", "free energy (IWB-FE-LBM)"],
+        "precision": "fp32 populations", "parallelism": "replicas",
+        "l2": "inputs larger than L2 (1.2 GB of populations per model)",
+    }
+
+
+def make_rho0(size):
+    from paper_2403_11167_gb300 import inputs, lbm
+
+    _, th = lbm.lbm_resolve_params(lbm.lbm_params_default(0, a=0.25, Tr=0.85, tau_nu=0.8))
+    return inputs.spinodal_noise(size, size, 0.5 * (th.rho_l + th.rho_v), 0.01, seed=2403)
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+
+def oracle_mlups(rho0, seconds, crop=512):
+    """Time the FP64 oracle, as it stands, on a crop of the workload: both models, the
+    number of steps grown until about ``seconds`` of CPU work."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2403_11167_gb300 import lbm
+
+    sub = np.ascontiguousarray(rho0[:crop, :crop])
+    updates, elapsed, steps = 0, 0.0, 1
+    cfgs = []
+    for model in (0, 1):
+        rp, th = lbm.lbm_resolve_params(lbm.lbm_params_default(model, a=0.25, Tr=0.85, tau_nu=0.8))
+        cfgs.append(O.make_params(a=rp.a, b=rp.b, R=rp.R, T=th.T, tau_e=rp.tau_e, tau_zeta=rp.tau_zeta,
+                                  tau_q=rp.tau_q, tau_j=rp.tau_j, tau_nu=rp.tau_nu, kappa_P=rp.kappa_P,
+                                  kappa_Li=rp.kappa_Li, sigma_Li=rp.sigma_Li, kappa=rp.kappa))
+    while elapsed < seconds:
+        for model in (0, 1):
+            f = O.init(model, sub)
+            t = time.perf_counter()
+            O.run(model, cfgs[model], f, steps)
+            elapsed += time.perf_counter() - t
+            updates += sub.size * steps
+        steps *= 2
+    return updates / elapsed / 1e6, O.num_threads(), f"{crop}x{crop} crop of the workload, both models, " \
+        f"{updates // sub.size} lattice steps in total, FP64"
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    rho0 = make_rho0(args.size)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_mlups(rho0, per_step / 4)
+    vals, cores, sample = [], 1, ""
+    for _ in range(args.steps):
+        v, cores, sample = oracle_mlups(rho0, per_step)
+        vals.append(v)
+    value = sum(vals) / len(vals)
+    cell_updates = 2 * args.lbm_steps * args.size * args.size
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cell_updates / (value * 1e6) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2403_11167_gb300", "csrc", "lbm_kernels.cuh"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if it was taken
+    on the current kernel source (matching hash); else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernels_ncu.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"kernel_source_sha256_12:\s*([0-9a-f]{12})", text)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"traffic_per_launch_4096\[{kernel}\]:\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) if m else None
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_2403_11167_gb300 import lbm
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    size, nsteps = args.size, args.lbm_steps
+    ncell = size * size
+    rho0 = make_rho0(size)
+    stream = torch.cuda.Stream()
+    ctxs = []
+    for model in (0, 1):
+        p = lbm.lbm_params_default(model, precision=lbm.LBM_F32, a=0.25, Tr=0.85, tau_nu=0.8)
+        ctxs.append(lbm.Context(p, size, size, stream=stream))
+    rho0_dev = torch.from_numpy(rho0.astype(np.float32)).cuda()
+    rho0_pinned = torch.from_numpy(rho0).pin_memory()
+    rho0_pinned_np = rho0_pinned.numpy()
+
+    def one_step(events=None):
+        for m, ctx in enumerate(ctxs):
+            ctx.set_density_device(rho0_dev)
+            if events is not None:
+                events[m][0].record(stream)
+            ctx.step(nsteps)
+            if events is not None:
+                events[m][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+        barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        barrier()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(2)]
+               for _ in range(args.steps)]
+        t0.record(stream)
+        for k in range(args.steps):
+            one_step(kev[k])
+        t1.record(stream)
+        barrier()
+        clocks = sampler.stop()
+        elapsed_ms = t0.elapsed_time(t1)
+        per_model_ms = [sum(kev[k][m][0].elapsed_time(kev[k][m][1]) for k in range(args.steps)) for m in range(2)]
+
+    elapsed = torch.tensor([elapsed_ms], device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(elapsed, op=torch.distributed.ReduceOp.MAX)
+    elapsed_ms = float(elapsed.item())
+    updates = ws * args.steps * 2 * nsteps * ncell
+    value = updates / (elapsed_ms * 1e-3) / 1e6
+
+    # end to end through the public API: pinned host rho0 -> H2D -> steps -> observables D2H
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            for ctx in ctxs:
+                ctx.set_density(rho0_pinned_np)
+                ctx.step(nsteps)
+                ctx.observables(0)
+        barrier()
+        e2e_s = time.perf_counter() - t
+        t_all = torch.tensor([e2e_s], device="cuda")
+        if ws > 1:
+            torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t_all.item())
+        e2e = {"value": updates / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 2 * ncell * 8,
+               "d2h_bytes_per_step": 2 * 8 * 8}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    names = ["pp_step_kernel", "fe_step_kernel"]
+    per_launch_s = [ms * 1e-3 / (args.steps * nsteps) for ms in per_model_ms]
+    dom = int(np.argmax(per_model_ms))
+    peak, peak_kind = measured_peak_gbs()
+    achieved = BYTES_PER_CELL_F32 * ncell / per_launch_s[dom] / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(names[dom]), "kernel": names[dom], "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": BYTES_PER_CELL_F32 * ncell}
+    per_model = {}
+    for m, key in enumerate(("pseudopotential", "free_energy")):
+        per_model[key] = {"mlups": ncell / per_launch_s[m] / 1e6, "us_per_launch": per_launch_s[m] * 1e6,
+                          "gbs_at_72B": BYTES_PER_CELL_F32 * ncell / per_launch_s[m] / 1e9,
+                          "frac_of_hbm": BYTES_PER_CELL_F32 * ncell / per_launch_s[m] / 1e9 / peak}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        v, cores, sample = oracle_mlups(rho0, args.cpu_seconds)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": args.steps * (2 + 2 * nsteps), "clocks": clocks, "per_model": per_model,
+        "kernel_source_sha256_12": kernel_source_hash(),
+    }
+    print(json.dumps(line))
+    for ctx in ctxs:
+        ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

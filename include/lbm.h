@@ -1,0 +1,198 @@
+/*
+ * lbm.h -- C ABI of the GB300 D2Q9 multiphase lattice Boltzmann library.
+ *
+ * Implements the two models compared in "Fundamental comparison between the
+ * pseudopotential and the free energy lattice Boltzmann methods" (Czelusniak,
+ * Martins, Cabezas Gomez, Bulgarelli, Monte Verde, de Castro; arXiv:2403.11167):
+ *
+ *   LBM_PSEUDOPOTENTIAL  the modified pseudopotential model (MP-LBM, Sec. 4):
+ *                        Eq. (1) MRT step with the Carnahan-Starling EOS (Eq. 28),
+ *                        psi of Eq. (11), Shan-Chen force Eq. (10), width-control
+ *                        source Eqs. (13), (30), (31) and forcing Eq. (32);
+ *   LBM_FREE_ENERGY      the improved well-balanced free-energy model (Sec. 2.2):
+ *                        Eq. (1) MRT step with chemical potential mu = mu_b - kappa
+ *                        lap rho (Eq. 29, stencils of Eq. 24), equilibrium Eq. (20)
+ *                        and forcing Eq. (21), with A = 0 and no gravity.
+ *
+ * Units are lattice units: dx = dt = c = 1, c_s^2 = 1/3, G = -1 (Sec. 2.1).
+ *
+ * Conventions for every function below:
+ *   - return value: LBM_OK (0) or a negative LBM_ERR_* code; no exception or
+ *     abort crosses the ABI; lbm_strerror() names a code.
+ *   - host pointers are owned by the caller and only read or written during the
+ *     call; the library keeps no caller pointer.
+ *   - device memory of a context is either allocated by the library (cudaMalloc)
+ *     or supplied by the caller as one workspace (lbm_workspace_bytes); a
+ *     context never frees a caller workspace.
+ *   - all GPU work of a context runs on the context's stream, in call order.
+ *     Functions that return host data synchronise that stream first.
+ *   - populations are stored as 9 planes f_i[y][x] (structure of arrays) of the
+ *     context precision; host-side population arrays use the velocity order of
+ *     Eq. (2) (0 rest, 1..4 = (1,0),(0,1),(-1,0),(0,-1), 5..8 = (1,1),(-1,1),
+ *     (-1,-1),(1,-1)), shape [9][ny][nx], row-major, FP64.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)          /* invalid argument (size, tau <= 1/2, Tr outside (0,1), ...) */
+#define LBM_ERR_UNSUPPORTED (-2)  /* feature not built (walls, A != 0, ...) */
+#define LBM_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define LBM_ERR_DIVERGED (-4)     /* NaN/Inf or rho <= 0 seen; sticky for the context */
+#define LBM_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
+#define LBM_ERR_NOCONVERGE (-6)   /* a host Newton/bisection solve failed */
+#define LBM_ERR_STATE (-7)        /* call out of order (e.g. step before set_density) */
+#define LBM_ERR_IO (-8)           /* checkpoint file could not be read or written */
+
+typedef enum { LBM_PSEUDOPOTENTIAL = 0, LBM_FREE_ENERGY = 1 } lbm_model;
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL_ZOUHE = 1 } lbm_bc;
+typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_precision;
+typedef enum { LBM_GEOMETRY_FLAT = 0, LBM_GEOMETRY_DROPLET = 1 } lbm_geometry;
+
+/* Model parameters (Eqs. 3, 28, 30-32, 20-21).  A NaN or non-positive entry
+ * where noted means "derive / use the default"; lbm_resolve_params fills them.
+ *   a, b, R     Carnahan-Starling EOS constants (Eq. 28); T = Tr * T_c(a, b, R).
+ *   Tr          reduced temperature, 0 < Tr < 1.
+ *   tau_nu      shear relaxation time (> 1/2).  Other taus <= 0 take the defaults
+ *               (both models: tau_rho = tau_j = 1):
+ *                 pseudopotential: tau_e = tau_zeta = tau_nu, tau_q = 1/1.99 (Sec. 5.1);
+ *                 free energy:     tau_e = 1/4 + tau_nu/2 (same bulk viscosity as the
+ *                                  pseudopotential model, Eqs. 9 and 23), tau_zeta = tau_q = 1.
+ *   kappa_P     interface-width factor of Eqs. (30)-(32); NaN -> 1.
+ *   kappa_Li    surface-tension factor of Eq. (30b); NaN -> 0.
+ *   sigma_Li    Li's coexistence parameter of Eq. (32); NaN -> the Appendix-B theory
+ *               value (eps = -16 G sigma_Li from Eq. S13 at the Maxwell densities).
+ *   match_kappa > 0: derive kappa_P and kappa_Li so that the pseudopotential model
+ *               has the interface width and surface tension of the free-energy model
+ *               with kappa = match_kappa (Sec. 3, Appendix B, Eqs. 26, S44, S46).
+ *   kappa       free-energy gradient coefficient (mu = mu_b - kappa lap rho); NaN -> 0.5.
+ *   A           viscosity-tuning term of Eq. (20); only A = 0 is supported.
+ *   body_fx/fy  constant body force added to the total force of either model. */
+typedef struct {
+    int model;       /* lbm_model */
+    int precision;   /* lbm_precision */
+    double a, b, R, Tr;
+    double tau_nu, tau_e, tau_zeta, tau_q, tau_j;
+    double kappa_P, kappa_Li, sigma_Li, match_kappa;
+    double kappa, A;
+    double body_fx, body_fy;
+} lbm_params;
+
+/* Thermodynamic and theoretical quantities derived on the host (FP64). */
+typedef struct {
+    double T, Tc, rho_c, p_c;      /* temperature, critical point (dp/drho = d2p/drho2 = 0) */
+    double rho_v, rho_l, p0;       /* Maxwell coexistence (equal p and mu_b; Eq. S12) */
+    double eps;                    /* -16 G sigma_Li used by the pseudopotential model */
+    double width, gamma;           /* planar tangent width and surface tension of the model's
+                                      continuum profile (Eq. 26 / Eq. S44, Eq. 25 / Eq. S46) */
+} lbm_thermo;
+
+/* Observables of the current state (see lbm_observables). */
+typedef struct {
+    double rho_l, rho_v;   /* probe means, liquid and vapour */
+    double width;          /* tangent interface width */
+    double dp;             /* p_EOS(rho_l) - p_EOS(rho_v) */
+    double u_max;          /* max |u| over the lattice (u of Eq. 6b) */
+    double mass;           /* sum of rho (FP64 accumulation) */
+    double radius;         /* equimolar radius (droplet), NaN for flat */
+    long long step;        /* time steps taken since lbm_set_density */
+    int status;            /* LBM_OK or LBM_ERR_DIVERGED */
+    int pad_;
+} lbm_obs;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill *p with the defaults of a model (a = 0.5, b = 4, R = 1, Tr = 0.8, tau_nu = 1,
+ * every derivable field NaN, precision FP32).  Never fails for a valid model. */
+int lbm_params_default(int model, lbm_params* p);
+
+/* Host-only (no GPU): resolve defaults and derived parameters of *in into *out and
+ * fill *th (either may alias nothing; out and th must be non-NULL).  Follows
+ * Sec. 3 and Appendix B: critical point, Maxwell densities, sigma_Li by Newton's
+ * method with Simpson quadrature of Eqs. (S13)-(S14) from eps = 2, and the
+ * optional width/surface-tension match.  Errors: LBM_ERR_ARG for invalid inputs,
+ * LBM_ERR_NOCONVERGE if a solve fails, LBM_ERR_UNSUPPORTED for A != 0. */
+int lbm_resolve_params(const lbm_params* in, lbm_params* out, lbm_thermo* th);
+
+/* Bytes of device workspace a context of this size and precision needs. */
+size_t lbm_workspace_bytes(int precision, int nx, int ny);
+
+/* Create a context for an nx x ny lattice (nx, ny >= 1; only periodic boundaries:
+ * any other bc returns LBM_ERR_UNSUPPORTED).  stream: a cudaStream_t to run on, or
+ * NULL for a stream the context creates and owns.  workspace: NULL to let the
+ * library cudaMalloc its memory, or a device pointer (256-byte aligned) of at least
+ * lbm_workspace_bytes(...) bytes that stays owned by the caller and must outlive
+ * the context.  Parameters are resolved as in lbm_resolve_params.  Launches no
+ * kernel.  *out is NULL on error. */
+int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_y, void* stream,
+               void* workspace, size_t workspace_bytes, lbm_ctx** out);
+
+/* Resolved parameters and thermodynamics of a context (host copies). */
+int lbm_derived(const lbm_ctx* ctx, lbm_params* resolved, lbm_thermo* th);
+
+/* Initialise f = f^eq(rho0, u = 0) of the model (Secs. 5.3-5.4: runs start from the
+ * equilibrium).  rho0: host, ny*nx doubles, row-major, every entry > 0 and below the
+ * EOS packing limit 4/b (else LBM_ERR_ARG).  Resets the step counter and status. */
+int lbm_set_density(lbm_ctx* ctx, const double* rho0);
+
+/* Same, rho0 already on the device (ny*nx values of the context precision). */
+int lbm_set_density_device(lbm_ctx* ctx, const void* rho0_device);
+
+/* Set / read the raw populations (host, FP64, [9][ny][nx], Eq. 2 order). */
+int lbm_set_populations(lbm_ctx* ctx, const double* f);
+int lbm_get_populations(lbm_ctx* ctx, double* f);
+
+/* Advance nsteps time steps (Eq. 1: collision and streaming).  Asynchronous: kernels
+ * are enqueued (CUDA-graph replays of 64-step chunks plus single launches) and the
+ * call returns.  Returns LBM_ERR_DIVERGED if a previous observables call saw a
+ * diverged state, LBM_ERR_STATE before lbm_set_density. */
+int lbm_step(lbm_ctx* ctx, long long nsteps);
+
+/* Observables of the current state for a flat slab (geometry 0) or a centred droplet
+ * (geometry 1).  Probes: flat -- columns {nx/2-1, nx/2} (liquid) and {0, nx-1}
+ * (vapour); droplet -- the 4x4 block at (nx/2-2, ny/2-2) and the four 4x4 corner
+ * blocks.  width = (rho_l - rho_v)/max |(rho[x+1]-rho[x-1])/2| along row 0 (flat) or
+ * ny/2 (droplet); dp = p_EOS(rho_l) - p_EOS(rho_v); radius = sqrt(sum(rho - rho_v)/
+ * (pi (rho_l - rho_v))).  Sets obs->status and the context status to
+ * LBM_ERR_DIVERGED on NaN/Inf or rho <= 0.  Synchronises the stream. */
+int lbm_observables(lbm_ctx* ctx, int geometry, lbm_obs* out);
+
+/* Macroscopic fields of the current state (host, FP64, ny*nx each, row-major):
+ * rho (Eq. 6a) and u including the half-force shift (Eq. 6b).  Any may be NULL. */
+int lbm_get_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* Populations f_i(x) (Eq. 2 order, FP64) of n cells (xs[k], ys[k]) into out[9 k + i]:
+ * a few hundred values, for probing very large lattices without a full download. */
+int lbm_get_populations_at(lbm_ctx* ctx, int n, const int* xs, const int* ys, double* out);
+
+/* Device pointer of the current population buffer (9 planes, context precision) and
+ * its plane pitch in elements (plane p starts at p * pitch). */
+int lbm_device_populations(lbm_ctx* ctx, void** f, long long* plane_pitch);
+
+/* Checkpoint: write/read the populations, step counter and parameters (binary). */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx* ctx, const char* path);
+
+/* The stream a context runs on (cudaStream_t). */
+void* lbm_stream(const lbm_ctx* ctx);
+
+void lbm_destroy(lbm_ctx* ctx);
+const char* lbm_strerror(int status);
+
+/* Library build information: "sm_103a ..." string. */
+const char* lbm_build_info(void);
+
+/* Text of the last CUDA failure behind an LBM_ERR_CUDA on this host thread. */
+const char* lbm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -247,7 +247,8 @@ static int pp_fields(const orc_params* p, int nx, int ny, const double* f, doubl
                      double* psi, double* Fx, double* Fy, double* ux, double* uy) {
     size_t N = (size_t)nx * ny;
     int bad = 0;
-    for (size_t c = 0; c < N; ++c) {
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (long c = 0; c < (long)N; ++c) {
         double s = 0.0;
         for (int i = 0; i < Q9; ++i) s += f[(size_t)i * N + c];
         rho[c] = s;
@@ -255,6 +256,7 @@ static int pp_fields(const orc_params* p, int nx, int ny, const double* f, doubl
         if (psi[c] < 0.0 || !(s > 0.0)) bad = 1;
     }
     if (bad) return -1;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;
@@ -360,17 +362,22 @@ static int fe_fields(const orc_params* p, int nx, int ny, const double* f, doubl
                      double* mu, double* Fx, double* Fy, double* ux, double* uy, double* drx,
                      double* dry) {
     size_t N = (size_t)nx * ny;
-    for (size_t c = 0; c < N; ++c) {
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (long c = 0; c < (long)N; ++c) {
         double s = 0.0;
         for (int i = 0; i < Q9; ++i) s += f[(size_t)i * N + c];
         rho[c] = s;
-        if (!(s > 0.0) || !(p->b * s / 4.0 < 1.0)) return -1;
+        if (!(s > 0.0) || !(p->b * s / 4.0 < 1.0)) bad = 1;
     }
+    if (bad) return -1;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;
             mu[c] = mu_bulk(p, rho[c]) - p->kappa * stencil_lap(rho, nx, ny, x, y);
         }
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;

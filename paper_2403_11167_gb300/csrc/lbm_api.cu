@@ -1,0 +1,629 @@
+// lbm_api.cu -- C ABI of the single-lattice solver (contexts, stepping, observables).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+#include "thermo.h"
+
+namespace {
+
+thread_local char g_cuda_msg[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+    snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s: %s", what, cudaGetErrorString(e));
+    return LBM_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+constexpr int kTXf = 128;  // columns per CTA, FP32
+constexpr int kTXd = 64;   // columns per CTA, FP64
+constexpr int kGraphSteps = 64;
+constexpr int kRedBlocks = 304;  // observables partial-reduction blocks (2 x 152 SMs)
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_params prm;
+    lbm_thermo th;
+    int nx, ny, prec;
+    size_t esz;
+    long long pitch;
+    char* ws;
+    bool own_ws;
+    void* f[2];
+    int cur;
+    void* fields;        // 4 N reals: rho, aux, ux, uy
+    double* partials;    // kRedBlocks x 3
+    double* d_obs;       // 8 doubles
+    double* h_pinned;    // 8 doubles, pinned
+    cudaStream_t stream;
+    bool own_stream;
+    cudaGraphExec_t graph[2];
+    long long step;
+    int status;
+    bool ready;
+    int rows;
+    lbmk::StepParams<float> spf;
+    lbmk::StepParams<double> spd;
+};
+
+extern "C" const char* lbm_last_cuda_error(void) { return g_cuda_msg; }
+
+extern "C" const char* lbm_strerror(int s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_UNSUPPORTED: return "unsupported feature";
+        case LBM_ERR_CUDA: return "CUDA runtime error";
+        case LBM_ERR_DIVERGED: return "simulation diverged (NaN/Inf or rho <= 0)";
+        case LBM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case LBM_ERR_NOCONVERGE: return "host solve did not converge";
+        case LBM_ERR_STATE: return "call out of order";
+        case LBM_ERR_IO: return "checkpoint I/O error";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* lbm_build_info(void) {
+    return "gb300 D2Q9 multiphase LBM; sm_103a; fused pull collide+stream; "
+           "pseudopotential (MP-LBM) and improved well-balanced free energy";
+}
+
+extern "C" int lbm_params_default(int model, lbm_params* p) {
+    if (!p || (model != LBM_PSEUDOPOTENTIAL && model != LBM_FREE_ENERGY)) return LBM_ERR_ARG;
+    const double nan = std::nan("");
+    p->model = model;
+    p->precision = LBM_F32;
+    p->a = 0.5;
+    p->b = 4.0;
+    p->R = 1.0;
+    p->Tr = 0.8;
+    p->tau_nu = 1.0;
+    p->tau_e = p->tau_zeta = p->tau_q = p->tau_j = 0.0;
+    p->kappa_P = p->kappa_Li = p->sigma_Li = nan;
+    p->match_kappa = 0.0;
+    p->kappa = nan;
+    p->A = 0.0;
+    p->body_fx = p->body_fy = 0.0;
+    return LBM_OK;
+}
+
+extern "C" int lbm_resolve_params(const lbm_params* in, lbm_params* out, lbm_thermo* th) {
+    if (!in || !out || !th) return LBM_ERR_ARG;
+    lbm_params p = *in;
+    if (p.model != LBM_PSEUDOPOTENTIAL && p.model != LBM_FREE_ENERGY) return LBM_ERR_ARG;
+    if (p.precision != LBM_F32 && p.precision != LBM_F64) return LBM_ERR_ARG;
+    if (!(p.a > 0 && p.b > 0 && p.R > 0 && p.Tr > 0 && p.Tr < 1)) return LBM_ERR_ARG;
+    if (!(p.tau_nu > 0.5)) return LBM_ERR_ARG;
+    if (p.A != 0.0) return LBM_ERR_UNSUPPORTED;
+    if (!std::isfinite(p.body_fx) || !std::isfinite(p.body_fy)) return LBM_ERR_ARG;
+    const bool pp = p.model == LBM_PSEUDOPOTENTIAL;
+    if (!(p.tau_j > 0)) p.tau_j = 1.0;
+    if (pp) {
+        if (!(p.tau_e > 0)) p.tau_e = p.tau_nu;
+        if (!(p.tau_zeta > 0)) p.tau_zeta = p.tau_nu;
+        if (!(p.tau_q > 0)) p.tau_q = 1.0 / 1.99;
+    } else {
+        if (!(p.tau_e > 0)) p.tau_e = 0.25 + 0.5 * p.tau_nu;
+        if (!(p.tau_zeta > 0)) p.tau_zeta = 1.0;
+        if (!(p.tau_q > 0)) p.tau_q = 1.0;
+    }
+    if (!(p.tau_e > 0.5 && p.tau_zeta > 0.5 && p.tau_q > 0.5 && p.tau_j > 0.5)) return LBM_ERR_ARG;
+    if (std::isnan(p.kappa)) p.kappa = 0.5;
+    lbm_host::CS eos{p.a, p.b, p.R};
+    lbm_thermo t;
+    std::memset(&t, 0, sizeof(t));
+    int rc = lbm_host::critical(eos, &t.rho_c, &t.Tc, &t.p_c);
+    if (rc) return rc;
+    t.T = p.Tr * t.Tc;
+    rc = lbm_host::maxwell(eos, t.T, &t.rho_v, &t.rho_l, &t.p0);
+    if (rc) return rc;
+    if (pp) {
+        if (std::isnan(p.sigma_Li)) {
+            rc = lbm_host::li_epsilon(eos, t.T, t.rho_v, t.rho_l, t.p0, &t.eps);
+            if (rc) return rc;
+            p.sigma_Li = t.eps / 16.0;  // eps = -16 G sigma_Li, G = -1
+        } else {
+            t.eps = 16.0 * p.sigma_Li;
+        }
+        if (p.match_kappa > 0) {
+            double Wfe, gfe, W1, g1;
+            rc = lbm_host::fe_theory(eos, t.T, t.rho_v, t.rho_l, t.p0, p.match_kappa, &Wfe, &gfe);
+            if (rc) return rc;
+            rc = lbm_host::pp_theory(eos, t.T, t.rho_v, t.rho_l, t.p0, t.eps, 1.0, 0.0, &W1, &g1);
+            if (rc) return rc;
+            p.kappa_P = (Wfe / W1) * (Wfe / W1);  // Eq. (S44): W ~ sqrt(kappa_P)
+            double Wk, gk;
+            rc = lbm_host::pp_theory(eos, t.T, t.rho_v, t.rho_l, t.p0, t.eps, p.kappa_P, 0.0, &Wk, &gk);
+            if (rc) return rc;
+            p.kappa_Li = p.kappa_P - gfe / (gk / p.kappa_P);  // Eq. (S46) linear in (kappa_P - kappa_Li)
+        }
+        if (std::isnan(p.kappa_P)) p.kappa_P = 1.0;
+        if (std::isnan(p.kappa_Li)) p.kappa_Li = 0.0;
+        rc = lbm_host::pp_theory(eos, t.T, t.rho_v, t.rho_l, t.p0, t.eps, p.kappa_P, p.kappa_Li, &t.width, &t.gamma);
+        if (rc) return rc;
+        if (!(p.kappa_P > 0)) return LBM_ERR_ARG;
+        // psi must exist over the coexistence range (radicand of Eq. 11 non-negative)
+        for (int k = 0; k <= 64; ++k) {
+            const double r = t.rho_v + (t.rho_l - t.rho_v) * k / 64.0;
+            if (!(r / 3.0 - eos.p(r, t.T) >= 0.0)) return LBM_ERR_ARG;
+        }
+    } else {
+        if (std::isnan(p.kappa_P)) p.kappa_P = 1.0;
+        if (std::isnan(p.kappa_Li)) p.kappa_Li = 0.0;
+        if (std::isnan(p.sigma_Li)) p.sigma_Li = 0.0;
+        if (!(p.kappa > 0)) return LBM_ERR_ARG;
+        t.eps = 0.0;
+        rc = lbm_host::fe_theory(eos, t.T, t.rho_v, t.rho_l, t.p0, p.kappa, &t.width, &t.gamma);
+        if (rc) return rc;
+    }
+    *out = p;
+    *th = t;
+    return LBM_OK;
+}
+
+static long long plane_pitch(int nx, int ny) {
+    const long long n = (long long)nx * ny;
+    return (n + 63) / 64 * 64;  // 256-byte aligned planes for FP32, 512 for FP64
+}
+
+extern "C" size_t lbm_workspace_bytes(int precision, int nx, int ny) {
+    if (nx < 1 || ny < 1) return 0;
+    const size_t esz = precision == LBM_F64 ? 8 : 4;
+    const size_t n = (size_t)nx * ny;
+    const size_t fbytes = align256(9 * (size_t)plane_pitch(nx, ny) * esz);
+    const size_t fields = align256(4 * n * esz);
+    return 2 * fbytes + fields + align256(kRedBlocks * 3 * sizeof(double)) + align256(8 * sizeof(double));
+}
+
+template <typename real>
+static void fill_step_params(lbmk::StepParams<real>& s, const lbm_ctx* c) {
+    const lbm_params& p = c->prm;
+    s.nx = c->nx;
+    s.ny = c->ny;
+    s.rows = c->rows;
+    s.pitch = c->pitch;
+    s.RT = (real)(p.R * c->th.T);
+    s.a = (real)p.a;
+    s.b4 = (real)(0.25 * p.b);
+    const double G = -1.0;
+    const double C1 = 5.0 / 6.0 * (p.kappa_P - 1.0), C2 = 0.5 * (1.0 - p.kappa_P);
+    s.kA = (real)(G * (C1 - C2 / 3.0));
+    s.kB = (real)(G * (C2 + 0.5 * p.kappa_Li));
+    s.li = (real)(12.0 * p.kappa_P * p.sigma_Li);
+    s.kappa = (real)p.kappa;
+    s.s_e = (real)(1.0 / p.tau_e);
+    s.s_z = (real)(1.0 / p.tau_zeta);
+    s.s_q = (real)(1.0 / p.tau_q);
+    s.s_nu = (real)(1.0 / p.tau_nu);
+    s.fx = (real)p.body_fx;
+    s.fy = (real)p.body_fy;
+}
+
+static int choose_rows(int nx, int ny, int tx) {
+    // Enough CTAs to fill 152 SMs several times over, but long strips so the y halo
+    // (recomputed rows) stays a few percent.
+    const long long gx = (nx + tx - 1) / tx;
+    const long long target = 152LL * 8;
+    long long rows = (ny * gx + target - 1) / target;
+    if (rows < 8) rows = 8;
+    if (rows > 64) rows = 64;
+    if (rows > ny) rows = ny;
+    return (int)rows;
+}
+
+extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_y, void* stream, void* workspace,
+                          size_t workspace_bytes, lbm_ctx** out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!p || nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31)) return LBM_ERR_ARG;
+    if (bc_x != LBM_BC_PERIODIC || bc_y != LBM_BC_PERIODIC) return LBM_ERR_UNSUPPORTED;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_ARG;
+    int rc = lbm_resolve_params(p, &c->prm, &c->th);
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    c->nx = nx;
+    c->ny = ny;
+    c->prec = c->prm.precision;
+    c->esz = c->prec == LBM_F64 ? 8 : 4;
+    c->pitch = plane_pitch(nx, ny);
+    c->rows = choose_rows(nx, ny, c->prec == LBM_F64 ? kTXd : kTXf);
+    const size_t need = lbm_workspace_bytes(c->prec, nx, ny);
+    if (workspace) {
+        if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+            delete c;
+            return LBM_ERR_ARG;
+        }
+        c->ws = static_cast<char*>(workspace);
+        c->own_ws = false;
+    } else {
+        cudaError_t e = cudaMalloc(&c->ws, need);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "cudaMalloc(workspace)");
+        }
+        c->own_ws = true;
+    }
+    const size_t fbytes = align256(9 * (size_t)c->pitch * c->esz);
+    const size_t n = (size_t)nx * ny;
+    c->f[0] = c->ws;
+    c->f[1] = c->ws + fbytes;
+    c->fields = c->ws + 2 * fbytes;
+    c->partials = reinterpret_cast<double*>(c->ws + 2 * fbytes + align256(4 * n * c->esz));
+    c->d_obs = reinterpret_cast<double*>(reinterpret_cast<char*>(c->partials) + align256(kRedBlocks * 3 * sizeof(double)));
+    cudaError_t e = cudaMallocHost(&c->h_pinned, 8 * sizeof(double));
+    if (e != cudaSuccess) {
+        if (c->own_ws) cudaFree(c->ws);
+        delete c;
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    if (stream) {
+        c->stream = static_cast<cudaStream_t>(stream);
+        c->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaFreeHost(c->h_pinned);
+            if (c->own_ws) cudaFree(c->ws);
+            delete c;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        c->own_stream = true;
+    }
+    c->graph[0] = c->graph[1] = nullptr;
+    c->cur = 0;
+    c->step = 0;
+    c->status = LBM_OK;
+    c->ready = false;
+    fill_step_params(c->spf, c);
+    fill_step_params(c->spd, c);
+    *out = c;
+    return LBM_OK;
+}
+
+extern "C" void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 2; ++i)
+        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->own_ws) cudaFree(c->ws);
+    delete c;
+}
+
+extern "C" void* lbm_stream(const lbm_ctx* c) { return c ? static_cast<void*>(c->stream) : nullptr; }
+
+extern "C" int lbm_derived(const lbm_ctx* c, lbm_params* resolved, lbm_thermo* th) {
+    if (!c) return LBM_ERR_ARG;
+    if (resolved) *resolved = c->prm;
+    if (th) *th = c->th;
+    return LBM_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Kernel launches
+
+static int launch_step(lbm_ctx* c, int src) {
+    const void* fin = c->f[src];
+    void* fout = c->f[src ^ 1];
+    const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
+    if (c->prec == LBM_F32) {
+        dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
+        if (pp)
+            lbmk::pp_step_kernel<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf);
+        else
+            lbmk::fe_step_kernel<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf);
+    } else {
+        dim3 grid((c->nx + kTXd - 1) / kTXd, (c->ny + c->rows - 1) / c->rows);
+        if (pp)
+            lbmk::pp_step_kernel<double, kTXd><<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd);
+        else
+            lbmk::fe_step_kernel<double, kTXd><<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd);
+    }
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+static int build_graph(lbm_ctx* c, int parity) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = LBM_OK;
+    int src = parity;
+    for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) {
+        rc = launch_step(c, src);
+        src ^= 1;
+    }
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return LBM_OK;
+}
+
+extern "C" int lbm_step(lbm_ctx* c, long long nsteps) {
+    if (!c || nsteps < 0) return LBM_ERR_ARG;
+    if (!c->ready) return LBM_ERR_STATE;
+    if (c->status) return c->status;
+    while (nsteps > 0) {
+        if (nsteps >= kGraphSteps) {
+            if (!c->graph[c->cur]) {
+                int rc = build_graph(c, c->cur);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+            nsteps -= kGraphSteps;
+            c->step += kGraphSteps;  // even count: buffer parity unchanged
+        } else {
+            int rc = launch_step(c, c->cur);
+            if (rc) return rc;
+            c->cur ^= 1;
+            --nsteps;
+            ++c->step;
+        }
+    }
+    return LBM_OK;
+}
+
+template <typename src_t>
+static int launch_init(lbm_ctx* c, const src_t* rho0_dev) {
+    const int model = c->prm.model;
+    if (c->prec == LBM_F32)
+        lbmk::init_kernel<float, src_t>
+            <<<kRedBlocks, 256, 0, c->stream>>>(rho0_dev, (float*)c->f[0], model, c->nx, c->ny, c->pitch);
+    else
+        lbmk::init_kernel<double, src_t>
+            <<<kRedBlocks, 256, 0, c->stream>>>(rho0_dev, (double*)c->f[0], model, c->nx, c->ny, c->pitch);
+    CK(cudaGetLastError());
+    c->cur = 0;
+    c->step = 0;
+    c->status = LBM_OK;
+    c->ready = true;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_density(lbm_ctx* c, const double* rho0) {
+    if (!c || !rho0) return LBM_ERR_ARG;
+    const size_t n = (size_t)c->nx * c->ny;
+    const double top = 4.0 / c->prm.b;
+    for (size_t k = 0; k < n; ++k)
+        if (!(rho0[k] > 0.0 && rho0[k] < top)) return LBM_ERR_ARG;
+    // stage the FP64 densities in the fields scratch (>= 8 N bytes), convert in the kernel
+    CK(cudaMemcpyAsync(c->fields, rho0, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    return launch_init(c, static_cast<const double*>(c->fields));
+}
+
+extern "C" int lbm_set_density_device(lbm_ctx* c, const void* rho0) {
+    if (!c || !rho0) return LBM_ERR_ARG;
+    if (c->prec == LBM_F32) return launch_init(c, static_cast<const float*>(rho0));
+    return launch_init(c, static_cast<const double*>(rho0));
+}
+
+// Host view f_i(x) (state after streaming, Eq. 2 order) <-> stored S_i(y) = f_i(y + c_i).
+static const int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int kCY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static inline size_t shifted(int x, int y, int i, int nx, int ny) {
+    int xs = (x + kCX[i] + nx) % nx, ys = (y + kCY[i] + ny) % ny;
+    return (size_t)ys * nx + xs;
+}
+
+extern "C" int lbm_set_populations(lbm_ctx* c, const double* f) {
+    if (!c || !f) return LBM_ERR_ARG;
+    const size_t n = (size_t)c->nx * c->ny;
+    std::vector<char> stage(n * c->esz);
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 9; ++i) {
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                const double v = f[i * n + shifted(x, y, i, c->nx, c->ny)];
+                const size_t k = (size_t)y * c->nx + x;
+                if (c->prec == LBM_F32)
+                    reinterpret_cast<float*>(stage.data())[k] = (float)v;
+                else
+                    reinterpret_cast<double*>(stage.data())[k] = v;
+            }
+        CK(cudaMemcpy(static_cast<char*>(c->f[0]) + (size_t)i * c->pitch * c->esz, stage.data(), n * c->esz,
+                      cudaMemcpyHostToDevice));
+    }
+    c->cur = 0;
+    c->step = 0;
+    c->status = LBM_OK;
+    c->ready = true;
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_populations(lbm_ctx* c, double* f) {
+    if (!c || !f) return LBM_ERR_ARG;
+    if (!c->ready) return LBM_ERR_STATE;
+    const size_t n = (size_t)c->nx * c->ny;
+    std::vector<char> stage(n * c->esz);
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 9; ++i) {
+        CK(cudaMemcpy(stage.data(), static_cast<char*>(c->f[c->cur]) + (size_t)i * c->pitch * c->esz, n * c->esz,
+                      cudaMemcpyDeviceToHost));
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                const size_t k = (size_t)y * c->nx + x;
+                const double v = c->prec == LBM_F32 ? (double)reinterpret_cast<const float*>(stage.data())[k]
+                                                    : reinterpret_cast<const double*>(stage.data())[k];
+                f[i * n + shifted(x, y, i, c->nx, c->ny)] = v;
+            }
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_populations_at(lbm_ctx* c, int n, const int* xs, const int* ys, double* out) {
+    if (!c || n < 0 || (n > 0 && (!xs || !ys || !out))) return LBM_ERR_ARG;
+    if (!c->ready) return LBM_ERR_STATE;
+    for (int k = 0; k < n; ++k)
+        if (xs[k] < 0 || xs[k] >= c->nx || ys[k] < 0 || ys[k] >= c->ny) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < n; ++k)
+        for (int i = 0; i < 9; ++i) {
+            // f_i(x) = S_i(x - c_i)
+            const int xs_ = (xs[k] - kCX[i] + c->nx) % c->nx, ys_ = (ys[k] - kCY[i] + c->ny) % c->ny;
+            const size_t off = ((size_t)i * c->pitch + (size_t)ys_ * c->nx + xs_) * c->esz;
+            if (c->prec == LBM_F32) {
+                float v;
+                CK(cudaMemcpy(&v, static_cast<char*>(c->f[c->cur]) + off, 4, cudaMemcpyDeviceToHost));
+                out[9 * k + i] = v;
+            } else {
+                CK(cudaMemcpy(&out[9 * k + i], static_cast<char*>(c->f[c->cur]) + off, 8, cudaMemcpyDeviceToHost));
+            }
+        }
+    return LBM_OK;
+}
+
+extern "C" int lbm_device_populations(lbm_ctx* c, void** f, long long* pitch) {
+    if (!c || !f) return LBM_ERR_ARG;
+    *f = c->f[c->cur];
+    if (pitch) *pitch = c->pitch;
+    return LBM_OK;
+}
+
+// rho, aux, ux, uy fields of the current state into the fields scratch.
+template <typename real>
+static int compute_fields(lbm_ctx* c, const lbmk::StepParams<real>& sp) {
+    const long long n = (long long)c->nx * c->ny;
+    real* rho = static_cast<real*>(c->fields);
+    real* aux = rho + n;
+    real* ux = aux + n;
+    real* uy = ux + n;
+    const real* f = static_cast<const real*>(c->f[c->cur]);
+    const int model = c->prm.model;
+    lbmk::rho_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(f, rho, aux, sp, model);
+    if (model == LBM_FREE_ENERGY) lbmk::mu_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
+    lbmk::velocity_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(f, rho, aux, ux, uy, sp, model);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+template <typename real>
+static int observables_impl(lbm_ctx* c, const lbmk::StepParams<real>& sp, int geometry, lbm_obs* o) {
+    int rc = compute_fields<real>(c, sp);
+    if (rc) return rc;
+    const long long n = (long long)c->nx * c->ny;
+    const real* rho = static_cast<const real*>(c->fields);
+    lbmk::obs_partial_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, rho + 2 * n, rho + 3 * n, n, c->partials);
+    lbmk::ObsConst C{c->nx, c->ny, geometry, kRedBlocks, c->prm.R * c->th.T, c->prm.a, 0.25 * c->prm.b};
+    lbmk::obs_final_kernel<real><<<1, 256, 0, c->stream>>>(rho, c->partials, C, c->d_obs);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->h_pinned, c->d_obs, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double* h = c->h_pinned;
+    o->rho_l = h[0];
+    o->rho_v = h[1];
+    o->width = h[2];
+    o->dp = h[3];
+    o->u_max = h[4];
+    o->mass = h[5];
+    o->radius = h[6];
+    o->step = c->step;
+    o->pad_ = 0;
+    if (h[7] != 0.0 || !std::isfinite(h[5])) c->status = LBM_ERR_DIVERGED;
+    o->status = c->status;
+    return LBM_OK;
+}
+
+extern "C" int lbm_observables(lbm_ctx* c, int geometry, lbm_obs* out) {
+    if (!c || !out || (geometry != 0 && geometry != 1)) return LBM_ERR_ARG;
+    if (!c->ready) return LBM_ERR_STATE;
+    int rc = c->prec == LBM_F32 ? observables_impl<float>(c, c->spf, geometry, out)
+                                : observables_impl<double>(c, c->spd, geometry, out);
+    if (rc) return rc;
+    return out->status;
+}
+
+template <typename real>
+static int fields_impl(lbm_ctx* c, const lbmk::StepParams<real>& sp, double* rho, double* ux, double* uy) {
+    int rc = compute_fields<real>(c, sp);
+    if (rc) return rc;
+    const size_t n = (size_t)c->nx * c->ny;
+    std::vector<real> stage(n);
+    CK(cudaStreamSynchronize(c->stream));
+    double* outs[3] = {rho, ux, uy};
+    const int slot[3] = {0, 2, 3};
+    for (int k = 0; k < 3; ++k) {
+        if (!outs[k]) continue;
+        CK(cudaMemcpy(stage.data(), static_cast<const real*>(c->fields) + slot[k] * n, n * sizeof(real),
+                      cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) outs[k][i] = (double)stage[i];
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* ux, double* uy) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->ready) return LBM_ERR_STATE;
+    return c->prec == LBM_F32 ? fields_impl<float>(c, c->spf, rho, ux, uy) : fields_impl<double>(c, c->spd, rho, ux, uy);
+}
+
+// ----------------------------------------------------------------------------
+// Checkpoint: "LBMCKPT1", nx, ny, model, precision, step, params, f (FP64, Eq. 2 order).
+
+extern "C" int lbm_save(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_ERR_ARG;
+    if (!c->ready) return LBM_ERR_STATE;
+    const size_t n = (size_t)c->nx * c->ny;
+    std::vector<double> f(9 * n);
+    int rc = lbm_get_populations(c, f.data());
+    if (rc) return rc;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return LBM_ERR_IO;
+    const char magic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+    int hdr[4] = {c->nx, c->ny, c->prm.model, c->prec};
+    bool ok = std::fwrite(magic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof(int), 4, fp) == 4 &&
+              std::fwrite(&c->step, sizeof(long long), 1, fp) == 1 &&
+              std::fwrite(&c->prm, sizeof(lbm_params), 1, fp) == 1 &&
+              std::fwrite(f.data(), sizeof(double), f.size(), fp) == f.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : LBM_ERR_IO;
+}
+
+extern "C" int lbm_load(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_ERR_ARG;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return LBM_ERR_IO;
+    char magic[8];
+    int hdr[4];
+    long long step;
+    lbm_params prm;
+    const size_t n = (size_t)c->nx * c->ny;
+    std::vector<double> f(9 * n);
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMCKPT1", 8) == 0 &&
+              std::fread(hdr, sizeof(int), 4, fp) == 4 && std::fread(&step, sizeof(long long), 1, fp) == 1 &&
+              std::fread(&prm, sizeof(lbm_params), 1, fp) == 1;
+    if (ok && (hdr[0] != c->nx || hdr[1] != c->ny || hdr[2] != c->prm.model || hdr[3] != c->prec)) {
+        std::fclose(fp);
+        return LBM_ERR_ARG;
+    }
+    ok = ok && std::fread(f.data(), sizeof(double), f.size(), fp) == f.size();
+    std::fclose(fp);
+    if (!ok) return LBM_ERR_IO;
+    int rc = lbm_set_populations(c, f.data());
+    if (rc) return rc;
+    c->step = step;
+    return LBM_OK;
+}

@@ -1,0 +1,659 @@
+// lbm_kernels.cuh -- sm_103a kernels of the fused D2Q9 multiphase time step.
+//
+// Layout: populations are 9 planes f_i[y][x] (structure of arrays), plane i at
+// offset i * pitch, velocity order of Eq. (2).  Streaming is done by pulling:
+// the kernel reading buffer A gathers f_i(x - c_i) (the post-collision values of
+// the previous step), collides, and writes f*_i(x) to buffer B at x, so A is
+// read-only and B write-only inside a launch (ping-pong).  Periodic in x and y.
+//
+// Fusion: every quantity needed at neighbours (psi for the pseudopotential model,
+// rho and mu for the free-energy model) is recomputed from the pulled populations
+// inside the CTA that needs it, so the step moves only 9 loads + 9 stores of
+// populations per cell through HBM.  A CTA owns a strip of TX columns and walks
+// down `rows` rows; the per-row neighbour fields live in small shared-memory
+// rings (sliding window), and one extra warp computes the x-halo columns.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+// D2Q9, Eq. (2): 0 rest; 1 (1,0); 2 (0,1); 3 (-1,0); 4 (0,-1); 5 (1,1); 6 (-1,1); 7 (-1,-1); 8 (1,-1).
+
+template <typename real>
+struct StepParams {
+    int nx, ny, rows;  // lattice, rows per CTA
+    long long pitch;   // plane pitch (elements)
+    real RT, a, b4;    // Carnahan-Starling: R*T, a, b/4  (Eq. 28)
+    real kA, kB;       // Q tensor (Eq. 30): G (C1 - C2/3) and G (C2 + kappa_Li/2)
+    real li;           // 12 kappa_P sigma_Li  (Eq. 32, consistency term; G^2 = 1)
+    real kappa;        // free energy: mu = mu_b - kappa lap rho
+    real s_e, s_z, s_q, s_nu;  // relaxation rates 1/tau (Eq. 3); tau_rho, tau_j drop out
+    real fx, fy;       // body force
+};
+
+template <typename real>
+__device__ __forceinline__ real cs_pressure(real rho, real RT, real a, real b4) {
+    const real e = b4 * rho;
+    const real om = real(1) - e;
+    const real num = real(1) + e * (real(1) + e * (real(1) - e));
+    return rho * RT * num / (om * om * om) - a * rho * rho;
+}
+
+// Eq. (11) with G = -1: psi = sqrt(2 (rho c_s^2 - p_EOS)).  NaN for a negative radicand
+// (propagates into the populations and is caught by the divergence check).
+template <typename real>
+__device__ __forceinline__ real pseudo_psi(real rho, const StepParams<real>& P) {
+    return sqrt(real(2) * (rho * real(1.0 / 3.0) - cs_pressure(rho, P.RT, P.a, P.b4)));
+}
+
+// Eq. (29): mu_b = RT (3 - e)/(1 - e)^3 + RT ln rho + RT - 2 a rho, e = b rho / 4.
+template <typename real>
+__device__ __forceinline__ real mu_bulk(real rho, const StepParams<real>& P) {
+    const real e = P.b4 * rho;
+    const real om = real(1) - e;
+    return P.RT * ((real(3) - e) / (om * om * om) + log(rho) + real(1)) - real(2) * P.a * rho;
+}
+
+__device__ __forceinline__ int wrap_idx(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// Pulled populations of cell (x, r): v_i = f_i(x - c_i).  xm = x-1, xp = x+1 (wrapped);
+// om, o0, op = row offsets of rows r-1, r, r+1 (wrapped).
+template <typename real>
+__device__ __forceinline__ void pull9(const real* __restrict__ f, long long pitch, int x, int xm, int xp,
+                                      long long om, long long o0, long long op, real v[9]) {
+    v[0] = __ldg(f + 0 * pitch + o0 + x);
+    v[1] = __ldg(f + 1 * pitch + o0 + xm);
+    v[2] = __ldg(f + 2 * pitch + om + x);
+    v[3] = __ldg(f + 3 * pitch + o0 + xp);
+    v[4] = __ldg(f + 4 * pitch + op + x);
+    v[5] = __ldg(f + 5 * pitch + om + xm);
+    v[6] = __ldg(f + 6 * pitch + om + xp);
+    v[7] = __ldg(f + 7 * pitch + op + xp);
+    v[8] = __ldg(f + 8 * pitch + op + xm);
+}
+
+template <typename real>
+__device__ __forceinline__ real sum9(const real v[9]) {
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
+// f* = f + M^-1 dm for the moment increments dm (rho increment is zero); M^-1 of Eq. (S49).
+template <typename real>
+__device__ __forceinline__ void apply_dm(real v[9], real de, real dz, real djx, real dqx, real djy, real dqy,
+                                         real dpxx, real dpxy) {
+    const real A = -de * real(1.0 / 36.0) - dz * real(1.0 / 18.0);
+    const real B = de * real(1.0 / 18.0) + dz * real(1.0 / 36.0);
+    const real X1 = (djx - dqx) * real(1.0 / 6.0);
+    const real Y1 = (djy - dqy) * real(1.0 / 6.0);
+    const real X2 = djx * real(1.0 / 6.0) + dqx * real(1.0 / 12.0);
+    const real Y2 = djy * real(1.0 / 6.0) + dqy * real(1.0 / 12.0);
+    const real Pp = dpxx * real(0.25);
+    const real Z = dpxy * real(0.25);
+    v[0] += (dz - de) * real(1.0 / 9.0);
+    v[1] += A + X1 + Pp;
+    v[2] += A + Y1 - Pp;
+    v[3] += A - X1 + Pp;
+    v[4] += A - Y1 - Pp;
+    v[5] += B + X2 + Y2 + Z;
+    v[6] += B - X2 + Y2 - Z;
+    v[7] += B - X2 - Y2 + Z;
+    v[8] += B + X2 - Y2 - Z;
+}
+
+// ---------------------------------------------------------------------------------
+// Modified pseudopotential collision of one cell (Eqs. 1, 4, 6, 10, 13, 30-32).
+//   v  : pulled populations (in: f, out: f*)
+//   pc : psi at the cell; pn[i] : psi at x + c_i (i = 1..8)
+template <typename real>
+__device__ __forceinline__ void pp_collide(real v[9], real rho, real pc, const real pn[9],
+                                           const StepParams<real>& P) {
+    const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
+    // Eq. (10): F_int = -G psi sum_i omega_i psi(x + c_i) c_i, G = -1
+    const real Sx = (pn[1] - pn[3]) * w1 + ((pn[5] - pn[7]) + (pn[8] - pn[6])) * w2;
+    const real Sy = (pn[2] - pn[4]) * w1 + ((pn[5] - pn[7]) + (pn[6] - pn[8])) * w2;
+    const real Fix = pc * Sx, Fiy = pc * Sy;
+    const real Fx = Fix + P.fx, Fy = Fiy + P.fy;
+    // Eq. (30): Q_ab = psi sum_i omega_i C_iab (psi_i - psi), C2 term carrying G
+    const real d1 = pn[1] - pc, d2 = pn[2] - pc, d3 = pn[3] - pc, d4 = pn[4] - pc;
+    const real d5 = pn[5] - pc, d6 = pn[6] - pc, d7 = pn[7] - pc, d8 = pn[8] - pc;
+    const real dd = ((d5 + d6) + (d7 + d8)) * w2;
+    const real sxx = (d1 + d3) * w1 + dd;
+    const real syy = (d2 + d4) * w1 + dd;
+    const real sa = sxx + syy - dd;  // sum_i omega_i d_i
+    const real sxy = ((d5 - d6) + (d7 - d8)) * w2;
+    const real Qxx = pc * (P.kA * sa + P.kB * sxx);
+    const real Qyy = pc * (P.kA * sa + P.kB * syy);
+    const real Qxy = pc * (P.kB * sxy);
+    // Eq. (32) consistency term: 12 kappa_P sigma_Li |F_int|^2/psi^2 = li |S|^2 (G^2 = 1)
+    const real L = P.li * (Sx * Sx + Sy * Sy);
+    // Eq. (6b) and the moments m = M f (Eq. S48)
+    const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const real inv_rho = real(1) / rho;
+    const real ux = (jx + real(0.5) * Fx) * inv_rho;
+    const real uy = (jy + real(0.5) * Fy) * inv_rho;
+    const real sax = (v[1] + v[2]) + (v[3] + v[4]);
+    const real sdg = (v[5] + v[6]) + (v[7] + v[8]);
+    const real e = -real(4) * v[0] - sax + real(2) * sdg;
+    const real z = real(4) * v[0] - real(2) * sax + sdg;
+    const real qx = real(2) * (v[3] - v[1]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const real qy = real(2) * (v[4] - v[2]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const real pxx = (v[1] + v[3]) - (v[2] + v[4]);
+    const real pxy = (v[5] + v[7]) - (v[6] + v[8]);
+    const real uu = ux * ux + uy * uy;
+    const real uF = ux * Fx + uy * Fy;
+    const real trQ = Qxx + Qyy;
+    // m* - m = -L (m - m^eq) + (I - L/2) MF' + MC  (Eqs. 1, 4/S66, 32, 13)
+    const real de = -P.s_e * (e - rho * (real(3) * uu - real(2))) + (real(1) - real(0.5) * P.s_e) * real(6) * uF +
+                    P.s_e * (L + real(1.5) * trQ);
+    const real dz = -P.s_z * (z - rho * (real(1) - real(3) * uu)) - (real(1) - real(0.5) * P.s_z) * real(6) * uF -
+                    P.s_z * (L + real(1.5) * trQ);
+    const real dqx = -P.s_q * (qx + rho * ux) - (real(1) - real(0.5) * P.s_q) * Fx;
+    const real dqy = -P.s_q * (qy + rho * uy) - (real(1) - real(0.5) * P.s_q) * Fy;
+    const real dpxx = -P.s_nu * (pxx - rho * (ux * ux - uy * uy)) +
+                      (real(1) - real(0.5) * P.s_nu) * real(2) * (ux * Fx - uy * Fy) - P.s_nu * (Qxx - Qyy);
+    const real dpxy = -P.s_nu * (pxy - rho * ux * uy) + (real(1) - real(0.5) * P.s_nu) * (ux * Fy + uy * Fx) -
+                      P.s_nu * Qxy;
+    // j* - j = F exactly (tau_j drops out)
+    apply_dm(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+}
+
+// ---------------------------------------------------------------------------------
+// Improved well-balanced free-energy collision of one cell (Eqs. 1, 6, 20, 21, 24).
+//   mn[i] : mu at x + c_i, rn[i] : rho at x + c_i (i = 1..8)
+template <typename real>
+__device__ __forceinline__ void fe_collide(real v[9], real rho, const real mn[9], const real rn[9],
+                                           const StepParams<real>& P) {
+    const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
+    // Eq. (24) gradient with weights: d_a phi = 3 sum_i w_i phi_i c_ia
+    const real gmx = (mn[1] - mn[3]) * w1 + ((mn[5] - mn[7]) + (mn[8] - mn[6])) * w2;
+    const real gmy = (mn[2] - mn[4]) * w1 + ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2;
+    const real grx = (rn[1] - rn[3]) * w1 + ((rn[5] - rn[7]) + (rn[8] - rn[6])) * w2;
+    const real gry = (rn[2] - rn[4]) * w1 + ((rn[5] - rn[7]) + (rn[6] - rn[8])) * w2;
+    const real Fx = -rho * gmx + P.fx, Fy = -rho * gmy + P.fy;
+    const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const real inv_rho = real(1) / rho;
+    const real ux = (jx + real(0.5) * Fx) * inv_rho;
+    const real uy = (jy + real(0.5) * Fy) * inv_rho;
+    const real sax = (v[1] + v[2]) + (v[3] + v[4]);
+    const real sdg = (v[5] + v[6]) + (v[7] + v[8]);
+    const real e = -real(4) * v[0] - sax + real(2) * sdg;
+    const real z = real(4) * v[0] - real(2) * sax + sdg;
+    const real qx = real(2) * (v[3] - v[1]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const real qy = real(2) * (v[4] - v[2]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const real pxx = (v[1] + v[3]) - (v[2] + v[4]);
+    const real pxy = (v[5] + v[7]) - (v[6] + v[8]);
+    const real uu = ux * ux + uy * uy;
+    const real uF = ux * Fx + uy * Fy;
+    const real s = ux * grx + uy * gry;  // u . grad rho
+    const real Gx = Fx + grx * real(1.0 / 3.0), Gy = Fy + gry * real(1.0 / 3.0);  // F + c_s^2 grad rho
+    // M F_i of Eq. (21): (0, 6uF + 4s, -6uF - 4s, Fx, -Fx, Fy, -Fy, 2(uxGx - uyGy), uxGy + uyGx)
+    const real fe = real(6) * uF + real(4) * s;
+    // m^eq of Eq. (20): (rho, rho(-4 + 3uu), rho(4 - 3uu), rho u, -rho u, ..., rho(ux^2-uy^2), rho ux uy)
+    const real de = -P.s_e * (e - rho * (real(3) * uu - real(4))) + (real(1) - real(0.5) * P.s_e) * fe;
+    const real dz = -P.s_z * (z - rho * (real(4) - real(3) * uu)) - (real(1) - real(0.5) * P.s_z) * fe;
+    const real dqx = -P.s_q * (qx + rho * ux) - (real(1) - real(0.5) * P.s_q) * Fx;
+    const real dqy = -P.s_q * (qy + rho * uy) - (real(1) - real(0.5) * P.s_q) * Fy;
+    const real dpxx = -P.s_nu * (pxx - rho * (ux * ux - uy * uy)) +
+                      (real(1) - real(0.5) * P.s_nu) * real(2) * (ux * Gx - uy * Gy);
+    const real dpxy = -P.s_nu * (pxy - rho * ux * uy) + (real(1) - real(0.5) * P.s_nu) * (ux * Gy + uy * Gx);
+    apply_dm(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+}
+
+// Chemical potential at one cell from rho at the cell (rc) and its 8 neighbours (Eq. 24 Laplacian).
+template <typename real>
+__device__ __forceinline__ real fe_mu(real rc, const real rn[9], const StepParams<real>& P) {
+    const real lap = ((rn[1] + rn[2]) + (rn[3] + rn[4])) * real(2.0 / 3.0) +
+                     ((rn[5] + rn[6]) + (rn[7] + rn[8])) * real(1.0 / 6.0) - rc * real(10.0 / 3.0);
+    return mu_bulk(rc, P) - P.kappa * lap;
+}
+
+// ---------------------------------------------------------------------------------
+// Pseudopotential step.  Block = TX main threads (one column each) + one halo warp.
+template <typename real, int TX>
+__global__ void __launch_bounds__(TX + 32) pp_step_kernel(const real* __restrict__ fin, real* __restrict__ fout,
+                                                          const StepParams<real> P) {
+    __shared__ real s_psi[4][TX + 2];
+    const int nx = P.nx, ny = P.ny;
+    const long long pitch = P.pitch;
+    const int x0 = blockIdx.x * TX;
+    const int w = min(TX, nx - x0);
+    const int y0 = blockIdx.y * P.rows;
+    const int y1 = min(y0 + P.rows, ny);
+    const int t = threadIdx.x;
+    const bool is_main = t < TX;
+    bool has_col;
+    int x, sc;
+    if (is_main) {
+        has_col = t < w;
+        x = x0 + (has_col ? t : 0);
+        sc = t + 1;
+    } else {
+        const int lane = t - TX;
+        has_col = lane < 2;
+        x = lane == 0 ? wrap_idx(x0 - 1, nx) : wrap_idx(x0 + w, nx);
+        sc = lane == 0 ? 0 : w + 1;
+    }
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+
+    real cur[9], prv[9];
+    auto row_offsets = [&](int r, long long& om, long long& o0, long long& op) {
+        om = (long long)wrap_idx(r - 1, ny) * nx;
+        o0 = (long long)wrap_idx(r, ny) * nx;
+        op = (long long)wrap_idx(r + 1, ny) * nx;
+    };
+    if (has_col) {
+        long long om, o0, op;
+        row_offsets(y0 - 1, om, o0, op);
+        pull9(fin, pitch, x, xm, xp, om, o0, op, cur);
+    }
+#pragma unroll 1
+    for (int r = y0 - 1; r <= y1; ++r) {
+        real nxt[9];
+        const bool more = r < y1;
+        if (has_col && more) {
+            long long om, o0, op;
+            row_offsets(r + 1, om, o0, op);
+            pull9(fin, pitch, x, xm, xp, om, o0, op, nxt);
+        }
+        real rho = real(0);
+        if (has_col) {
+            rho = sum9(cur);
+            s_psi[r & 3][sc] = pseudo_psi(rho, P);
+        }
+        __syncthreads();
+        if (is_main && has_col && r > y0) {
+            // centre row c = r - 1: neighbours in rows c-1 (slot r-2), c (r-1), c+1 (r)
+            const real* sm = s_psi[(r - 2) & 3];
+            const real* s0 = s_psi[(r - 1) & 3];
+            const real* sp = s_psi[r & 3];
+            real pn[9];
+            pn[0] = s0[sc];
+            pn[1] = s0[sc + 1];
+            pn[2] = sp[sc];
+            pn[3] = s0[sc - 1];
+            pn[4] = sm[sc];
+            pn[5] = sp[sc + 1];
+            pn[6] = sp[sc - 1];
+            pn[7] = sm[sc - 1];
+            pn[8] = sm[sc + 1];
+            const real rho_c = sum9(prv);
+            pp_collide(prv, rho_c, pn[0], pn, P);
+            const long long o = (long long)(r - 1) * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fout[i * pitch + o] = prv[i];
+        }
+        if (has_col) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                prv[i] = cur[i];
+                cur[i] = nxt[i];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Free-energy step.  rho ring (8 rows, 2 halo columns each side), mu ring (4 rows, 1 halo).
+// Halo warp lanes: 0 -> x0-2, 1 -> x0-1 (also mu), 2 -> x0+w (also mu), 3 -> x0+w+1.
+template <typename real, int TX>
+__global__ void __launch_bounds__(TX + 32) fe_step_kernel(const real* __restrict__ fin, real* __restrict__ fout,
+                                                          const StepParams<real> P) {
+    __shared__ real s_rho[8][TX + 4];
+    __shared__ real s_mu[4][TX + 2];
+    const int nx = P.nx, ny = P.ny;
+    const long long pitch = P.pitch;
+    const int x0 = blockIdx.x * TX;
+    const int w = min(TX, nx - x0);
+    const int y0 = blockIdx.y * P.rows;
+    const int y1 = min(y0 + P.rows, ny);
+    const int t = threadIdx.x;
+    const bool is_main = t < TX;
+    bool has_col, has_mu;
+    int x, rc, mc;  // global column, rho-ring column, mu-ring column
+    if (is_main) {
+        has_col = t < w;
+        has_mu = has_col;
+        x = x0 + (has_col ? t : 0);
+        rc = t + 2;
+        mc = t + 1;
+    } else {
+        const int lane = t - TX;
+        has_col = lane < 4;
+        has_mu = lane == 1 || lane == 2;
+        const int off = lane == 0 ? -2 : lane == 1 ? -1 : lane == 2 ? w : w + 1;
+        x = wrap_idx(x0 + off, nx);
+        rc = lane == 0 ? 0 : lane == 1 ? 1 : lane == 2 ? w + 2 : w + 3;
+        mc = lane == 1 ? 0 : w + 1;
+    }
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+    auto row_offsets = [&](int r, long long& om, long long& o0, long long& op) {
+        om = (long long)wrap_idx(r - 1, ny) * nx;
+        o0 = (long long)wrap_idx(r, ny) * nx;
+        op = (long long)wrap_idx(r + 1, ny) * nx;
+    };
+    real p0[9], p1[9], p2[9];  // pulled populations of rows r-2, r-1, r
+    if (has_col) {
+        long long om, o0, op;
+        row_offsets(y0 - 2, om, o0, op);
+        pull9(fin, pitch, x, xm, xp, om, o0, op, p2);
+    }
+#pragma unroll 1
+    for (int r = y0 - 2; r <= y1 + 1; ++r) {
+        real nxt[9];
+        if (has_col && r <= y1) {
+            long long om, o0, op;
+            row_offsets(r + 1, om, o0, op);
+            pull9(fin, pitch, x, xm, xp, om, o0, op, nxt);
+        }
+        if (has_col) s_rho[r & 7][rc] = sum9(p2);
+        __syncthreads();
+        if (has_mu && r >= y0) {
+            // mu at row r - 1 from rho rows r-2, r-1, r
+            const real* rm = s_rho[(r - 2) & 7];
+            const real* r0 = s_rho[(r - 1) & 7];
+            const real* rp = s_rho[r & 7];
+            real rn[9];
+            rn[1] = r0[rc + 1];
+            rn[2] = rp[rc];
+            rn[3] = r0[rc - 1];
+            rn[4] = rm[rc];
+            rn[5] = rp[rc + 1];
+            rn[6] = rp[rc - 1];
+            rn[7] = rm[rc - 1];
+            rn[8] = rm[rc + 1];
+            s_mu[(r - 1) & 3][mc] = fe_mu(r0[rc], rn, P);
+        }
+        __syncthreads();
+        if (is_main && has_col && r >= y0 + 2) {
+            // centre row c = r - 2
+            const real* mm = s_mu[(r - 3) & 3];
+            const real* m0 = s_mu[(r - 2) & 3];
+            const real* mp = s_mu[(r - 1) & 3];
+            const real* rm = s_rho[(r - 3) & 7];
+            const real* r0 = s_rho[(r - 2) & 7];
+            const real* rp = s_rho[(r - 1) & 7];
+            real mn[9], rn[9];
+            mn[1] = m0[mc + 1]; mn[2] = mp[mc]; mn[3] = m0[mc - 1]; mn[4] = mm[mc];
+            mn[5] = mp[mc + 1]; mn[6] = mp[mc - 1]; mn[7] = mm[mc - 1]; mn[8] = mm[mc + 1];
+            rn[1] = r0[rc + 1]; rn[2] = rp[rc]; rn[3] = r0[rc - 1]; rn[4] = rm[rc];
+            rn[5] = rp[rc + 1]; rn[6] = rp[rc - 1]; rn[7] = rm[rc - 1]; rn[8] = rm[rc + 1];
+            const real rho_c = r0[rc];
+            fe_collide(p0, rho_c, mn, rn, P);
+            const long long o = (long long)(r - 2) * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
+        }
+        if (has_col) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                p0[i] = p1[i];
+                p1[i] = p2[i];
+                p2[i] = nxt[i];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Storage convention of the pull scheme: buffer S holds S_i(y) = f_i(y + c_i), i.e. the
+// population that the next step pulls into y + c_i.  The state f of the method is recovered
+// as f_i(x) = S_i(x - c_i).
+__device__ __forceinline__ long long shifted_cell(int x, int y, int cx, int cy, int nx, int ny) {
+    int xs = x + cx, ys = y + cy;
+    xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+    ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+    return (long long)ys * nx + xs;
+}
+
+// Pulled populations of cell (x, y): v_i = S_i(x - c_i) = f_i(x).
+template <typename real>
+__device__ __forceinline__ void pull_cell(const real* __restrict__ S, long long pitch, int x, int y, int nx, int ny,
+                                          real v[9]) {
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const long long om = (long long)(y == 0 ? ny - 1 : y - 1) * nx, o0 = (long long)y * nx,
+                    op = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
+    pull9(S, pitch, x, xm, xp, om, o0, op, v);
+}
+
+// f = f^eq(rho0, u = 0): Eq. (4) (weights w_i rho) or Eq. (20) (f_0 = rho, others 0),
+// stored as S_i(y) = f^eq_i(rho0(y + c_i)).
+template <typename real, typename src_t>
+__global__ void init_kernel(const src_t* __restrict__ rho0, real* __restrict__ S, int model, int nx, int ny,
+                            long long pitch) {
+    const int cxs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int cys[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const long long n = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx), y = (int)(c / nx);
+        if (model == 0) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const real w = i == 0 ? real(4.0 / 9.0) : (i < 5 ? real(1.0 / 9.0) : real(1.0 / 36.0));
+                S[i * pitch + c] = w * (real)rho0[shifted_cell(x, y, cxs[i], cys[i], nx, ny)];
+            }
+        } else {
+            S[c] = (real)rho0[c];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) S[i * pitch + c] = real(0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Macroscopic fields for observables (not on the time-stepping path).
+// rho of the current populations (Eq. 6a), and aux = psi (P) or rho itself (FE).
+template <typename real>
+__global__ void rho_kernel(const real* __restrict__ f, real* __restrict__ rho, real* __restrict__ aux,
+                           const StepParams<real> P, int model) {
+    const long long n = (long long)P.nx * P.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        real v[9];
+        pull_cell(f, P.pitch, (int)(c % P.nx), (int)(c / P.nx), P.nx, P.ny, v);
+        const real r = sum9(v);
+        rho[c] = r;
+        aux[c] = model == 0 ? pseudo_psi(r, P) : r;
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void gather8(const real* __restrict__ a, int x, int y, int nx, int ny, real n[9]) {
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const long long ym = (long long)(y == 0 ? ny - 1 : y - 1) * nx, y0 = (long long)y * nx,
+                    yp = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
+    n[0] = a[y0 + x];
+    n[1] = a[y0 + xp];
+    n[2] = a[yp + x];
+    n[3] = a[y0 + xm];
+    n[4] = a[ym + x];
+    n[5] = a[yp + xp];
+    n[6] = a[yp + xm];
+    n[7] = a[ym + xm];
+    n[8] = a[ym + xp];
+}
+
+// FE: mu from rho (writes into mu).
+template <typename real>
+__global__ void mu_kernel(const real* __restrict__ rho, real* __restrict__ mu, const StepParams<real> P) {
+    const long long n = (long long)P.nx * P.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % P.nx), y = (int)(c / P.nx);
+        real rn[9];
+        gather8(rho, x, y, P.nx, P.ny, rn);
+        mu[c] = fe_mu(rn[0], rn, P);
+    }
+}
+
+// u of Eq. (6b) with the model's total force; aux = psi (P) or mu (FE); rho field given.
+template <typename real>
+__global__ void velocity_kernel(const real* __restrict__ f, const real* __restrict__ rho,
+                                const real* __restrict__ aux, real* __restrict__ ux, real* __restrict__ uy,
+                                const StepParams<real> P, int model) {
+    const long long n = (long long)P.nx * P.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % P.nx), y = (int)(c / P.nx);
+        real v[9], an[9];
+        pull_cell(f, P.pitch, x, y, P.nx, P.ny, v);
+        gather8(aux, x, y, P.nx, P.ny, an);
+        const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
+        const real gx = (an[1] - an[3]) * w1 + ((an[5] - an[7]) + (an[8] - an[6])) * w2;
+        const real gy = (an[2] - an[4]) * w1 + ((an[5] - an[7]) + (an[6] - an[8])) * w2;
+        const real r = rho[c];
+        real Fx, Fy;
+        if (model == 0) {
+            Fx = an[0] * gx + P.fx;
+            Fy = an[0] * gy + P.fy;
+        } else {
+            Fx = -r * gx + P.fx;
+            Fy = -r * gy + P.fy;
+        }
+        const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+        const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+        ux[c] = (jx + real(0.5) * Fx) / r;
+        uy[c] = (jy + real(0.5) * Fy) / r;
+    }
+}
+
+// Block partials of the observables reduction: [mass, max|u|^2, bad count] per block.
+template <typename real>
+__global__ void obs_partial_kernel(const real* __restrict__ rho, const real* __restrict__ ux,
+                                   const real* __restrict__ uy, long long n, double* __restrict__ partials) {
+    double m = 0.0, u2 = 0.0, bad = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double r = (double)rho[c], a = (double)ux[c], b = (double)uy[c];
+        const double q = a * a + b * b;
+        if (!(r > 0.0) || !isfinite(r) || !isfinite(q)) bad += 1.0;
+        m += r;
+        u2 = fmax(u2, isfinite(q) ? q : 0.0);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m += __shfl_down_sync(0xffffffffu, m, o);
+        u2 = fmax(u2, __shfl_down_sync(0xffffffffu, u2, o));
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    __shared__ double sm[3][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sm[0][wid] = m;
+        sm[1][wid] = u2;
+        sm[2][wid] = bad;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        m = lane < nw ? sm[0][lane] : 0.0;
+        u2 = lane < nw ? sm[1][lane] : 0.0;
+        bad = lane < nw ? sm[2][lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            m += __shfl_down_sync(0xffffffffu, m, o);
+            u2 = fmax(u2, __shfl_down_sync(0xffffffffu, u2, o));
+            bad += __shfl_down_sync(0xffffffffu, bad, o);
+        }
+        if (lane == 0) {
+            partials[3 * blockIdx.x + 0] = m;
+            partials[3 * blockIdx.x + 1] = u2;
+            partials[3 * blockIdx.x + 2] = bad;
+        }
+    }
+}
+
+struct ObsConst {
+    int nx, ny, geometry, nblocks;
+    double RT, a, b4;
+};
+
+__device__ __forceinline__ double cs_p_d(double rho, const ObsConst& C) {
+    const double e = C.b4 * rho, om = 1.0 - e;
+    return rho * C.RT * (1.0 + e + e * e - e * e * e) / (om * om * om) - C.a * rho * rho;
+}
+
+// One block: combine partials, probe means, tangent width, pressure jump, radius.
+// out: [rho_l, rho_v, width, dp, u_max, mass, radius, bad]
+template <typename real>
+__global__ void obs_final_kernel(const real* __restrict__ rho, const double* __restrict__ partials, ObsConst C,
+                                 double* __restrict__ out) {
+    __shared__ double red[4][256];
+    const int t = threadIdx.x;
+    double m = 0.0, u2 = 0.0, bad = 0.0, liq = 0.0, vap = 0.0, dmax = 0.0;
+    for (int b = t; b < C.nblocks; b += blockDim.x) {
+        m += partials[3 * b];
+        u2 = fmax(u2, partials[3 * b + 1]);
+        bad += partials[3 * b + 2];
+    }
+    const int nx = C.nx, ny = C.ny;
+    double nl, nv;
+    if (C.geometry == 0) {
+        const int xl0 = nx / 2 - 1 < 0 ? 0 : nx / 2 - 1, xl1 = nx / 2, xv1 = nx - 1;
+        for (int y = t; y < ny; y += blockDim.x) {
+            liq += (double)rho[(long long)y * nx + xl0] + (double)rho[(long long)y * nx + xl1];
+            vap += (double)rho[(long long)y * nx + 0] + (double)rho[(long long)y * nx + xv1];
+        }
+        nl = nv = 2.0 * ny;
+    } else {
+        const int cx0 = nx / 2 - 2, cy0 = ny / 2 - 2;
+        if (t < 16) {
+            const int dx = t & 3, dy = t >> 2;
+            liq = (double)rho[(long long)wrap_idx(cy0 + dy, ny) * nx + wrap_idx(cx0 + dx, nx)];
+        }
+        if (t < 64) {
+            const int k = t >> 4, dx = t & 3, dy = (t >> 2) & 3;
+            const int xx = (k & 1) ? nx - 4 + dx : dx, yy = (k & 2) ? ny - 4 + dy : dy;
+            vap = (double)rho[(long long)wrap_idx(yy, ny) * nx + wrap_idx(xx, nx)];
+        }
+        nl = 16.0;
+        nv = 64.0;
+    }
+    const int prow = C.geometry == 0 ? 0 : ny / 2;
+    for (int x = t; x < nx; x += blockDim.x) {
+        const double a = (double)rho[(long long)prow * nx + (x == nx - 1 ? 0 : x + 1)];
+        const double b = (double)rho[(long long)prow * nx + (x == 0 ? nx - 1 : x - 1)];
+        dmax = fmax(dmax, fabs(a - b) * 0.5);
+    }
+    red[0][t] = m;
+    red[1][t] = liq;
+    red[2][t] = vap;
+    red[3][t] = bad;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s) {
+            red[0][t] += red[0][t + s];
+            red[1][t] += red[1][t + s];
+            red[2][t] += red[2][t + s];
+            red[3][t] += red[3][t + s];
+        }
+        __syncthreads();
+    }
+    const double msum = red[0][0], lsum = red[1][0], vsum = red[2][0], bsum = red[3][0];
+    __syncthreads();
+    red[0][t] = u2;
+    red[1][t] = dmax;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s) {
+            red[0][t] = fmax(red[0][t], red[0][t + s]);
+            red[1][t] = fmax(red[1][t], red[1][t + s]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double rl = lsum / nl, rv = vsum / nv;
+        out[0] = rl;
+        out[1] = rv;
+        out[2] = (rl - rv) / red[1][0];
+        out[3] = cs_p_d(rl, C) - cs_p_d(rv, C);
+        out[4] = sqrt(red[0][0]);
+        out[5] = msum;
+        const double ex = msum - rv * (double)nx * (double)ny;
+        out[6] = C.geometry == 1 ? sqrt(fmax(ex, 0.0) / (3.14159265358979323846 * (rl - rv))) : nan("");
+        out[7] = bsum;
+    }
+}
+
+}  // namespace lbmk

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of ``liblbm.so`` (the C ABI of ``include/lbm.h``).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Functions keep the C names.  ``Context`` is a convenience owner of a
+``lbm_ctx*`` whose device workspace is a PyTorch tensor (PyTorch provides device
+memory and the stream; nothing else).
+
+The library must have been built (``python -m paper_2403_11167_gb300.build`` or
+``__graft_entry__.build()``); importing this module without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+LBM_OK = 0
+LBM_ERR_ARG = -1
+LBM_ERR_UNSUPPORTED = -2
+LBM_ERR_CUDA = -3
+LBM_ERR_DIVERGED = -4
+LBM_ERR_TIMEOUT = -5
+LBM_ERR_NOCONVERGE = -6
+LBM_ERR_STATE = -7
+LBM_ERR_IO = -8
+
+LBM_PSEUDOPOTENTIAL = 0
+LBM_FREE_ENERGY = 1
+LBM_F32 = 0
+LBM_F64 = 1
+LBM_BC_PERIODIC = 0
+FLAT = 0
+DROPLET = 1
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("precision", ctypes.c_int)] + [
+        (n, ctypes.c_double) for n in (
+            "a", "b", "R", "Tr", "tau_nu", "tau_e", "tau_zeta", "tau_q", "tau_j",
+            "kappa_P", "kappa_Li", "sigma_Li", "match_kappa", "kappa", "A", "body_fx", "body_fy")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lbm_thermo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("T", "Tc", "rho_c", "p_c", "rho_v", "rho_l", "p0", "eps", "width", "gamma")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lbm_obs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("rho_l", "rho_v", "width", "dp", "u_max", "mass", "radius")] + [
+        ("step", ctypes.c_longlong), ("status", ctypes.c_int), ("pad_", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = f"{what}: {lbm_strerror(code)} ({code})"
+        if code == LBM_ERR_CUDA:
+            msg += " -- " + _lib().lbm_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2403_11167_gb300.build` "
+                               "(the library has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, T, O = ctypes.POINTER(lbm_params), ctypes.POINTER(lbm_thermo), ctypes.POINTER(lbm_obs)
+        dp, vp = ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+        sig = {
+            "lbm_params_default": ([ctypes.c_int, P], ctypes.c_int),
+            "lbm_resolve_params": ([P, P, T], ctypes.c_int),
+            "lbm_workspace_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+            "lbm_create": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_size_t,
+                            ctypes.POINTER(vp)], ctypes.c_int),
+            "lbm_derived": ([vp, P, T], ctypes.c_int),
+            "lbm_set_density": ([vp, dp], ctypes.c_int),
+            "lbm_set_density_device": ([vp, vp], ctypes.c_int),
+            "lbm_set_populations": ([vp, dp], ctypes.c_int),
+            "lbm_get_populations": ([vp, dp], ctypes.c_int),
+            "lbm_step": ([vp, ctypes.c_longlong], ctypes.c_int),
+            "lbm_observables": ([vp, ctypes.c_int, O], ctypes.c_int),
+            "lbm_get_fields": ([vp, dp, dp, dp], ctypes.c_int),
+            "lbm_get_populations_at": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp],
+                                       ctypes.c_int),
+            "lbm_device_populations": ([vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+            "lbm_save": ([vp, ctypes.c_char_p], ctypes.c_int),
+            "lbm_load": ([vp, ctypes.c_char_p], ctypes.c_int),
+            "lbm_stream": ([vp], vp),
+            "lbm_destroy": ([vp], None),
+            "lbm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "lbm_build_info": ([], ctypes.c_char_p),
+            "lbm_last_cuda_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _L = L
+    return _L
+
+
+def lib():
+    return _lib()
+
+
+def _check(rc, what):
+    if rc != LBM_OK:
+        raise LBMError(rc, what)
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def lbm_strerror(code: int) -> str:
+    return _lib().lbm_strerror(code).decode()
+
+
+def lbm_build_info() -> str:
+    return _lib().lbm_build_info().decode()
+
+
+def lbm_params_default(model: int, **overrides) -> lbm_params:
+    p = lbm_params()
+    _check(_lib().lbm_params_default(model, ctypes.byref(p)), "lbm_params_default")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def lbm_resolve_params(p: lbm_params):
+    out, th = lbm_params(), lbm_thermo()
+    _check(_lib().lbm_resolve_params(ctypes.byref(p), ctypes.byref(out), ctypes.byref(th)), "lbm_resolve_params")
+    return out, th
+
+
+def lbm_workspace_bytes(precision: int, nx: int, ny: int) -> int:
+    return int(_lib().lbm_workspace_bytes(precision, nx, ny))
+
+
+class Context:
+    """Owner of one ``lbm_ctx``.  The workspace is a torch uint8 CUDA tensor and the
+    stream a torch stream (its handle is passed to the library)."""
+
+    def __init__(self, params: lbm_params, nx: int, ny: int, stream=None, device="cuda"):
+        import torch
+
+        self.nx, self.ny = nx, ny
+        self.torch = torch
+        nbytes = lbm_workspace_bytes(params.precision, nx, ny)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        handle = ctypes.c_void_p()
+        rc = _lib().lbm_create(ctypes.byref(params), nx, ny, LBM_BC_PERIODIC, LBM_BC_PERIODIC,
+                               ctypes.c_void_p(self.stream.cuda_stream), ctypes.c_void_p(aligned),
+                               ctypes.c_size_t(nbytes), ctypes.byref(handle))
+        _check(rc, "lbm_create")
+        self.h = handle
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def derived(self):
+        p, th = lbm_params(), lbm_thermo()
+        _check(_lib().lbm_derived(self.h, ctypes.byref(p), ctypes.byref(th)), "lbm_derived")
+        return p, th
+
+    def set_density(self, rho0: np.ndarray):
+        rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+        assert rho0.shape == (self.ny, self.nx)
+        _check(_lib().lbm_set_density(self.h, _dptr(rho0)), "lbm_set_density")
+
+    def set_density_device(self, rho0_tensor):
+        _check(_lib().lbm_set_density_device(self.h, ctypes.c_void_p(rho0_tensor.data_ptr())),
+               "lbm_set_density_device")
+
+    def set_populations(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9, self.ny, self.nx)
+        _check(_lib().lbm_set_populations(self.h, _dptr(f)), "lbm_set_populations")
+
+    def populations(self) -> np.ndarray:
+        f = np.zeros((9, self.ny, self.nx))
+        _check(_lib().lbm_get_populations(self.h, _dptr(f)), "lbm_get_populations")
+        return f
+
+    def populations_at(self, xs, ys) -> np.ndarray:
+        xs = np.ascontiguousarray(xs, dtype=np.int32)
+        ys = np.ascontiguousarray(ys, dtype=np.int32)
+        out = np.zeros((len(xs), 9))
+        ip = ctypes.POINTER(ctypes.c_int)
+        _check(_lib().lbm_get_populations_at(self.h, len(xs), xs.ctypes.data_as(ip), ys.ctypes.data_as(ip),
+                                             _dptr(out)), "lbm_get_populations_at")
+        return out
+
+    def step(self, n: int):
+        _check(_lib().lbm_step(self.h, int(n)), "lbm_step")
+
+    def observables(self, geometry: int = FLAT) -> dict:
+        o = lbm_obs()
+        rc = _lib().lbm_observables(self.h, geometry, ctypes.byref(o))
+        if rc not in (LBM_OK, LBM_ERR_DIVERGED):
+            _check(rc, "lbm_observables")
+        return o.as_dict()
+
+    def fields(self):
+        n = self.nx * self.ny
+        rho, ux, uy = (np.zeros(n) for _ in range(3))
+        _check(_lib().lbm_get_fields(self.h, _dptr(rho), _dptr(ux), _dptr(uy)), "lbm_get_fields")
+        s = (self.ny, self.nx)
+        return rho.reshape(s), ux.reshape(s), uy.reshape(s)
+
+    def device_populations(self):
+        p = ctypes.c_void_p()
+        pitch = ctypes.c_longlong()
+        _check(_lib().lbm_device_populations(self.h, ctypes.byref(p), ctypes.byref(pitch)), "lbm_device_populations")
+        return p.value, pitch.value
+
+    def save(self, path: str):
+        _check(_lib().lbm_save(self.h, path.encode()), "lbm_save")
+
+    def load(self, path: str):
+        _check(_lib().lbm_load(self.h, path.encode()), "lbm_load")
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+
+def nan():
+    return math.nan

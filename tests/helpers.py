@@ -1,0 +1,25 @@
+"""Shared test helpers: build a GPU context and the matching oracle parameters."""
+import numpy as np
+
+import oracle as O
+
+
+def oracle_params(rp, th):
+    """Oracle parameters equal to a resolved ``lbm_params`` (rp) and its thermodynamics (th)."""
+    return O.make_params(a=rp.a, b=rp.b, R=rp.R, T=th.T, tau_rho=1.0, tau_e=rp.tau_e, tau_zeta=rp.tau_zeta,
+                         tau_q=rp.tau_q, tau_j=rp.tau_j, tau_nu=rp.tau_nu, kappa_P=rp.kappa_P,
+                         kappa_Li=rp.kappa_Li, sigma_Li=rp.sigma_Li, kappa=rp.kappa, fx=rp.body_fx,
+                         fy=rp.body_fy)
+
+
+def gpu_context(model, precision, nx, ny, **kw):
+    from paper_2403_11167_gb300 import lbm
+
+    p = lbm.lbm_params_default(model, precision=precision, **kw)
+    ctx = lbm.Context(p, nx, ny)
+    rp, th = ctx.derived()
+    return ctx, rp, th
+
+
+def max_rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())

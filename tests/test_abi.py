@@ -1,0 +1,86 @@
+"""CPU checks of the C ABI library: it loads, exports every declared symbol, and its
+host-only parameter derivation agrees with the oracle's thermodynamics."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import thermo
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2403_11167_gb300 import lbm
+
+    return lbm
+
+
+def _declared_functions():
+    names = set()
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 20
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("a,Tr", [(0.5, 0.8), (0.25, 0.6), (0.25, 0.85), (0.5, 0.95), (0.25, 0.5)])
+def test_resolve_params_matches_oracle_thermo(lib, model, a, Tr):
+    out, th = lib.lbm_resolve_params(lib.lbm_params_default(model, a=a, Tr=Tr))
+    rv, rl, p0 = thermo.maxwell(a, 4.0, 1.0, Tr)
+    rc, Tc, pc = thermo.critical_point(a, 4.0, 1.0)
+    assert abs(th.Tc / Tc - 1) < 1e-13 and abs(th.rho_c / rc - 1) < 1e-12
+    assert abs(th.rho_v / rv - 1) < 1e-11 and abs(th.rho_l / rl - 1) < 1e-12 and abs(th.p0 / p0 - 1) < 1e-11
+    if model == 0:
+        sig, eps, _ = thermo.sigma_li(a, 4.0, 1.0, Tr)
+        assert abs(out.sigma_Li / sig - 1) < 1e-11
+        assert out.tau_e == out.tau_nu and abs(out.tau_q - 1 / 1.99) < 1e-15
+        _, eps, _ = thermo.sigma_li(a, 4.0, 1.0, Tr)
+        assert abs(th.width / thermo.pp_width(a, 4.0, 1.0, Tr, 1.0, eps) - 1) < 1e-4
+    else:
+        assert abs(out.tau_e - 0.75) < 1e-15 and out.kappa == 0.5
+        assert abs(th.width / thermo.fe_width(a, 4.0, 1.0, Tr, 0.5) - 1) < 1e-4
+        assert abs(th.gamma / thermo.fe_surface_tension(a, 4.0, 1.0, Tr, 0.5) - 1) < 1e-4
+
+
+def test_match_to_free_energy(lib):
+    """Sec. 3 / App. B: kappa_P and kappa_Li reproducing the FE width and surface tension."""
+    out, th = lib.lbm_resolve_params(lib.lbm_params_default(0, a=0.25, Tr=0.6, match_kappa=0.5))
+    m = thermo.match_pp_to_fe(0.25, 4.0, 1.0, 0.6, 0.5)
+    assert abs(out.kappa_P / m["kappa_P"] - 1) < 1e-5
+    assert abs(out.kappa_Li / m["kappa_Li"] - 1) < 1e-5
+    assert abs(th.width / m["W"] - 1) < 1e-4 and abs(th.gamma / m["gamma"] - 1) < 1e-4
+
+
+def test_argument_errors(lib):
+    bad = [dict(Tr=1.2), dict(Tr=0.0), dict(tau_nu=0.5), dict(a=-1.0), dict(tau_e=0.4)]
+    for kw in bad:
+        with pytest.raises(lib.LBMError) as e:
+            lib.lbm_resolve_params(lib.lbm_params_default(0, **kw))
+        assert e.value.code == lib.LBM_ERR_ARG
+    with pytest.raises(lib.LBMError) as e:
+        lib.lbm_resolve_params(lib.lbm_params_default(1, A=0.1))
+    assert e.value.code == lib.LBM_ERR_UNSUPPORTED
+    assert lib.lbm_strerror(lib.LBM_ERR_DIVERGED).startswith("simulation diverged")
+    assert lib.lbm_workspace_bytes(0, 0, 5) == 0
+    assert lib.lbm_workspace_bytes(1, 256, 4) > 2 * 9 * 256 * 4 * 8
+    assert "sm_103a" in lib.lbm_build_info()
