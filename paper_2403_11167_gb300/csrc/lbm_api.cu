@@ -206,6 +206,11 @@ static void fill_step_params(lbmk::StepParams<real>& s, const lbm_ctx* c) {
     s.kB = (real)(G * (C2 + 0.5 * p.kappa_Li));
     s.li = (real)(12.0 * p.kappa_P * p.sigma_Li);
     s.kappa = (real)p.kappa;
+    s.rho_ref_v = (real)c->th.rho_v;
+    s.rho_ref_l = (real)c->th.rho_l;
+    s.rho_split = (real)(0.5 * (c->th.rho_v + c->th.rho_l));
+    const lbm_host::CS eos{p.a, p.b, p.R};
+    s.mu_off_l = (real)(eos.mu((double)s.rho_ref_l, c->th.T) - eos.mu((double)s.rho_ref_v, c->th.T));
     s.s_e = (real)(1.0 / p.tau_e);
     s.s_z = (real)(1.0 / p.tau_zeta);
     s.s_q = (real)(1.0 / p.tau_q);

@@ -28,6 +28,8 @@ struct StepParams {
     real kA, kB;       // Q tensor (Eq. 30): G (C1 - C2/3) and G (C2 + kappa_Li/2)
     real li;           // 12 kappa_P sigma_Li  (Eq. 32, consistency term; G^2 = 1)
     real kappa;        // free energy: mu = mu_b - kappa lap rho
+    real rho_ref_v, rho_ref_l, rho_split;  // coexistence densities (reference points of mu_b) and midpoint
+    real mu_off_l;     // mu_b(rho_ref_l) - mu_b(rho_ref_v) at the rounded references (host FP64)
     real s_e, s_z, s_q, s_nu;  // relaxation rates 1/tau (Eq. 3); tau_rho, tau_j drop out
     real fx, fy;       // body force
 };
@@ -48,11 +50,23 @@ __device__ __forceinline__ real pseudo_psi(real rho, const StepParams<real>& P) 
 }
 
 // Eq. (29): mu_b = RT (3 - e)/(1 - e)^3 + RT ln rho + RT - 2 a rho, e = b rho / 4.
+// Only differences of mu enter the method (F = -rho grad mu), so the kernels use
+// mu_b(rho) - mu_b(rho_r) with rho_r the Maxwell density of the same phase
+// (mu_b(rho_v) = mu_b(rho_l)): one constant offset for every cell.  Written as a
+// divided difference it has no cancellation between the O(0.1) terms of Eq. (29),
+// which in FP32 would leave O(1e-8) noise on a chemical potential of O(1e-3):
+//   ln(rho/rho_r) = log1p(d/rho_r),  d = rho - rho_r,
+//   g(e) - g(e_r) = (e - e_r) [2 (ur^2 + ur u + u^2)/(u^3 ur^3) + (ur + u)/(u^2 ur^2)],
+// with g(e) = (3 - e)/(1 - e)^3 = 2/u^3 + 1/u^2, u = 1 - e.
 template <typename real>
-__device__ __forceinline__ real mu_bulk(real rho, const StepParams<real>& P) {
-    const real e = P.b4 * rho;
-    const real om = real(1) - e;
-    return P.RT * ((real(3) - e) / (om * om * om) + log(rho) + real(1)) - real(2) * P.a * rho;
+__device__ __forceinline__ real mu_bulk_rel(real rho, const StepParams<real>& P) {
+    const bool liq = rho >= P.rho_split;
+    const real rr = liq ? P.rho_ref_l : P.rho_ref_v;
+    const real d = rho - rr;
+    const real u = real(1) - P.b4 * rho, ur = real(1) - P.b4 * rr;
+    const real u2 = u * u, ur2 = ur * ur;
+    const real dg = P.b4 * d * (real(2) * (ur2 + ur * u + u2) / (u2 * u * ur2 * ur) + (ur + u) / (u2 * ur2));
+    return P.RT * (dg + log1p(d / rr)) - real(2) * P.a * d + (liq ? P.mu_off_l : real(0));
 }
 
 __device__ __forceinline__ int wrap_idx(int i, int n) {
@@ -205,12 +219,13 @@ __device__ __forceinline__ void fe_collide(real v[9], real rho, const real mn[9]
     apply_dm(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
 }
 
-// Chemical potential at one cell from rho at the cell (rc) and its 8 neighbours (Eq. 24 Laplacian).
+// Chemical potential (up to the constant mu_b(rho_v)) at one cell from rho at the cell (rc) and
+// its 8 neighbours; Eq. (24) Laplacian summed over differences.
 template <typename real>
 __device__ __forceinline__ real fe_mu(real rc, const real rn[9], const StepParams<real>& P) {
-    const real lap = ((rn[1] + rn[2]) + (rn[3] + rn[4])) * real(2.0 / 3.0) +
-                     ((rn[5] + rn[6]) + (rn[7] + rn[8])) * real(1.0 / 6.0) - rc * real(10.0 / 3.0);
-    return mu_bulk(rc, P) - P.kappa * lap;
+    const real lap = (((rn[1] - rc) + (rn[2] - rc)) + ((rn[3] - rc) + (rn[4] - rc))) * real(2.0 / 3.0) +
+                     (((rn[5] - rc) + (rn[6] - rc)) + ((rn[7] - rc) + (rn[8] - rc))) * real(1.0 / 6.0);
+    return mu_bulk_rel(rc, P) - P.kappa * lap;
 }
 
 // ---------------------------------------------------------------------------------
