@@ -176,6 +176,40 @@ int lbm_get_populations_at(lbm_ctx* ctx, int n, const int* xs, const int* ys, do
  * its plane pitch in elements (plane p starts at p * pitch). */
 int lbm_device_populations(lbm_ctx* ctx, void** f, long long* plane_pitch);
 
+/* Maximum number of reduction blocks lbm_observables_fields_static accepts. */
+#define LBM_STATIC_MAX_BLOCKS 1024
+
+/* Observables of caller-owned device fields without allocating any memory.
+ *
+ * The paper has no counterpart: this is a library service for callers that cannot
+ * call cudaMalloc -- for example a host process whose device memory is entirely
+ * reserved by another allocator (a framework's caching pool that owns the GPU), or
+ * a real-time loop that must not pay for an allocation or the implicit
+ * synchronisation one can cause.  Everything else in this library allocates its
+ * scratch inside a context workspace; this entry point needs no context.
+ *
+ * Inputs: rho, ux, uy -- device arrays of nx*ny values (row-major) of the given
+ * precision (LBM_F32 or LBM_F64), e.g. the fields a caller keeps itself.  a, b, R, T
+ * define the Carnahan-Starling pressure used for dp.  geometry and the probe, width,
+ * pressure-jump and radius definitions are those of lbm_observables.  nblocks:
+ * number of partial-reduction blocks, 1..LBM_STATIC_MAX_BLOCKS (else LBM_ERR_ARG).
+ * Output: out_dev -- caller-owned device array of 8 doubles, written with
+ * {rho_l, rho_v, width, dp, u_max, mass, radius, count of cells with NaN/Inf or
+ * rho <= 0}.  stream: cudaStream_t (NULL = legacy default stream); the call only
+ * enqueues work and returns.
+ *
+ * Scratch: a file-scope __device__ array of LBM_STATIC_MAX_BLOCKS * 3 doubles
+ * (24 KiB), present on every GPU that loads the library until the process exits.
+ * The first call on a device looks up that array's device address (with that device
+ * current) and caches it; make that first call before any stream capture on the
+ * device.  Every call shares the one array, which keeps the last call's partial
+ * sums: each call writes every slot it later reads, so nothing needs clearing, but
+ * calls that overlap on the GPU (different streams, no ordering) race and give wrong
+ * results.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+int lbm_observables_fields_static(int precision, const void* rho, const void* ux, const void* uy, int nx,
+                                  int ny, int geometry, double a, double b, double R, double T, int nblocks,
+                                  double* out_dev, void* stream);
+
 /* Checkpoint: write/read the populations, step counter and parameters (binary). */
 int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);

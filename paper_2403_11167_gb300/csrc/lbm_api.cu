@@ -586,6 +586,65 @@ extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* ux, double* uy) {
 }
 
 // ----------------------------------------------------------------------------
+// Observables of caller-owned device fields with no allocation: the partial sums of
+// the reduction live in a file-scope device array instead of a context workspace.
+
+static __device__ __align__(256) double g_static_partials[LBM_STATIC_MAX_BLOCKS * 3];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_static_ptr[kMaxDevices] = {nullptr};
+bool g_static_ready[kMaxDevices] = {false};
+}  // namespace
+
+// Device address of g_static_partials on the current device, looked up once per device
+// (the host-side symbol is only a stand-in and must never be passed to a kernel).
+static int static_partials_ptr(double** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return LBM_ERR_UNSUPPORTED;
+    if (!__atomic_load_n(&g_static_ready[dev], __ATOMIC_ACQUIRE)) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_static_partials));
+        g_static_ptr[dev] = static_cast<double*>(p);
+        __atomic_store_n(&g_static_ready[dev], true, __ATOMIC_RELEASE);
+    }
+    *out = g_static_ptr[dev];
+    return LBM_OK;
+}
+
+template <typename real>
+static int static_obs_impl(const real* rho, const real* ux, const real* uy, int nx, int ny, int geometry, double a,
+                           double b, double R, double T, int nblocks, double* out, cudaStream_t s) {
+    double* partials = nullptr;
+    int rc = static_partials_ptr(&partials);
+    if (rc) return rc;
+    const long long n = (long long)nx * ny;
+    lbmk::obs_partial_kernel<real><<<nblocks, 256, 0, s>>>(rho, ux, uy, n, partials);
+    lbmk::ObsConst C{nx, ny, geometry, nblocks, R * T, a, 0.25 * b};
+    lbmk::obs_final_kernel<real><<<1, 256, 0, s>>>(rho, partials, C, out);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+extern "C" int lbm_observables_fields_static(int precision, const void* rho, const void* ux, const void* uy, int nx,
+                                             int ny, int geometry, double a, double b, double R, double T,
+                                             int nblocks, double* out_dev, void* stream) {
+    if (!rho || !ux || !uy || !out_dev || nx < 1 || ny < 1 || (geometry != 0 && geometry != 1)) return LBM_ERR_ARG;
+    if (nblocks < 1 || nblocks > LBM_STATIC_MAX_BLOCKS) return LBM_ERR_ARG;
+    if (!(a > 0 && b > 0 && R > 0 && T > 0)) return LBM_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == LBM_F32)
+        return static_obs_impl<float>(static_cast<const float*>(rho), static_cast<const float*>(ux),
+                                      static_cast<const float*>(uy), nx, ny, geometry, a, b, R, T, nblocks, out_dev, s);
+    if (precision == LBM_F64)
+        return static_obs_impl<double>(static_cast<const double*>(rho), static_cast<const double*>(ux),
+                                       static_cast<const double*>(uy), nx, ny, geometry, a, b, R, T, nblocks, out_dev,
+                                       s);
+    return LBM_ERR_ARG;
+}
+
+// ----------------------------------------------------------------------------
 // Checkpoint: "LBMCKPT1", nx, ny, model, precision, step, params, f (FP64, Eq. 2 order).
 
 extern "C" int lbm_save(lbm_ctx* c, const char* path) {

@@ -102,6 +102,9 @@ def _lib():
             "lbm_get_populations_at": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp],
                                        ctypes.c_int),
             "lbm_device_populations": ([vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+            "lbm_observables_fields_static": ([ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, vp, vp], ctypes.c_int),
             "lbm_save": ([vp, ctypes.c_char_p], ctypes.c_int),
             "lbm_load": ([vp, ctypes.c_char_p], ctypes.c_int),
             "lbm_stream": ([vp], vp),
@@ -156,6 +159,17 @@ def lbm_resolve_params(p: lbm_params):
     out, th = lbm_params(), lbm_thermo()
     _check(_lib().lbm_resolve_params(ctypes.byref(p), ctypes.byref(out), ctypes.byref(th)), "lbm_resolve_params")
     return out, th
+
+
+LBM_STATIC_MAX_BLOCKS = 1024
+
+
+def lbm_observables_fields_static(precision, rho_ptr, ux_ptr, uy_ptr, nx, ny, geometry, a, b, R, T, nblocks,
+                                  out_ptr, stream_ptr):
+    """Marshal raw device pointers to the no-allocation observables entry point."""
+    return _lib().lbm_observables_fields_static(precision, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(ux_ptr),
+                                                ctypes.c_void_p(uy_ptr), nx, ny, geometry, a, b, R, T, nblocks,
+                                                ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream_ptr))
 
 
 def lbm_workspace_bytes(precision: int, nx: int, ny: int) -> int:
