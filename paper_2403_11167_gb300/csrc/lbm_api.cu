@@ -10,6 +10,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
+#include "step_tma.cuh"
 #include "thermo.h"
 
 namespace {
@@ -31,6 +32,7 @@ constexpr int kTXf = 128;  // columns per CTA, FP32
 constexpr int kTXd = 64;   // columns per CTA, FP64
 constexpr int kGraphSteps = 64;
 constexpr int kRedBlocks = 304;  // observables partial-reduction blocks (2 x 152 SMs)
+constexpr int kTmaStages = 6;    // row-pipeline depth of the TMA-fed FP32 kernels
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
@@ -49,6 +51,8 @@ struct lbm_ctx {
     void* fields;        // 4 N reals: rho, aux, ux, uy
     double* partials;    // kRedBlocks x 3
     double* d_obs;       // 8 doubles
+    int* d_err;          // device error word of the TMA kernels (bounded waits)
+    bool use_tma;
     double* h_pinned;    // 8 doubles, pinned
     cudaStream_t stream;
     bool own_stream;
@@ -187,7 +191,7 @@ extern "C" size_t lbm_workspace_bytes(int precision, int nx, int ny) {
     const size_t n = (size_t)nx * ny;
     const size_t fbytes = align256(9 * (size_t)plane_pitch(nx, ny) * esz);
     const size_t fields = align256(4 * n * esz);
-    return 2 * fbytes + fields + align256(kRedBlocks * 3 * sizeof(double)) + align256(8 * sizeof(double));
+    return 2 * fbytes + fields + align256(kRedBlocks * 3 * sizeof(double)) + align256(8 * sizeof(double)) + 256;
 }
 
 template <typename real>
@@ -273,6 +277,8 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->fields = c->ws + 2 * fbytes;
     c->partials = reinterpret_cast<double*>(c->ws + 2 * fbytes + align256(4 * n * c->esz));
     c->d_obs = reinterpret_cast<double*>(reinterpret_cast<char*>(c->partials) + align256(kRedBlocks * 3 * sizeof(double)));
+    c->d_err = reinterpret_cast<int*>(reinterpret_cast<char*>(c->d_obs) + align256(8 * sizeof(double)));
+    c->use_tma = c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 4 && std::getenv("LBM_NO_TMA") == nullptr;
     cudaError_t e = cudaMallocHost(&c->h_pinned, 8 * sizeof(double));
     if (e != cudaSuccess) {
         if (c->own_ws) cudaFree(c->ws);
@@ -330,7 +336,17 @@ static int launch_step(lbm_ctx* c, int src) {
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
-    if (c->prec == LBM_F32) {
+    if (c->use_tma) {
+        dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
+        if (pp)
+            lbmk::pp_step_tma<kTXf, kTmaStages>
+                <<<grid, kTXf + 32, sizeof(lbmk::PPTmaSmem<kTXf, kTmaStages>), c->stream>>>(
+                    (const float*)fin, (float*)fout, c->spf, c->d_err);
+        else
+            lbmk::fe_step_tma<kTXf, kTmaStages>
+                <<<grid, kTXf + 32, sizeof(lbmk::FETmaSmem<kTXf, kTmaStages>), c->stream>>>(
+                    (const float*)fin, (float*)fout, c->spf, c->d_err);
+    } else if (c->prec == LBM_F32) {
         dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
         if (pp)
             lbmk::pp_step_kernel<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf);
@@ -402,6 +418,7 @@ static int launch_init(lbm_ctx* c, const src_t* rho0_dev) {
         lbmk::init_kernel<double, src_t>
             <<<kRedBlocks, 256, 0, c->stream>>>(rho0_dev, (double*)c->f[0], model, c->nx, c->ny, c->pitch);
     CK(cudaGetLastError());
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     c->cur = 0;
     c->step = 0;
     c->status = LBM_OK;
@@ -452,6 +469,7 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f) {
         CK(cudaMemcpy(static_cast<char*>(c->f[0]) + (size_t)i * c->pitch * c->esz, stage.data(), n * c->esz,
                       cudaMemcpyHostToDevice));
     }
+    CK(cudaMemset(c->d_err, 0, sizeof(int)));
     c->cur = 0;
     c->step = 0;
     c->status = LBM_OK;
@@ -536,7 +554,10 @@ static int observables_impl(lbm_ctx* c, const lbmk::StepParams<real>& sp, int ge
     lbmk::obs_final_kernel<real><<<1, 256, 0, c->stream>>>(rho, c->partials, C, c->d_obs);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->h_pinned, c->d_obs, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (herr) c->status = LBM_ERR_TIMEOUT;
     const double* h = c->h_pinned;
     o->rho_l = h[0];
     o->rho_v = h[1];
@@ -547,7 +568,7 @@ static int observables_impl(lbm_ctx* c, const lbmk::StepParams<real>& sp, int ge
     o->radius = h[6];
     o->step = c->step;
     o->pad_ = 0;
-    if (h[7] != 0.0 || !std::isfinite(h[5])) c->status = LBM_ERR_DIVERGED;
+    if (c->status == LBM_OK && (h[7] != 0.0 || !std::isfinite(h[5]))) c->status = LBM_ERR_DIVERGED;
     o->status = c->status;
     return LBM_OK;
 }
