@@ -298,7 +298,7 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
-    names = ["pp_step_kernel", "fe_step_kernel"]
+    names = ["pp_step_tma", "fe_step_tma"]
     per_launch_s = [ms * 1e-3 / (args.steps * nsteps) for ms in per_model_ms]
     dom = int(np.argmax(per_model_ms))
     peak, peak_kind = measured_peak_gbs()

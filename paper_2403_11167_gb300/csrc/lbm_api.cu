@@ -28,11 +28,17 @@ int cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
     } while (0)
 
-constexpr int kTXf = 128;  // columns per CTA, FP32
+#ifndef LBM_TXF
+#define LBM_TXF 256
+#endif
+#ifndef LBM_TMA_STAGES
+#define LBM_TMA_STAGES 6
+#endif
+constexpr int kTXf = LBM_TXF;  // columns per CTA, FP32
 constexpr int kTXd = 64;   // columns per CTA, FP64
 constexpr int kGraphSteps = 64;
 constexpr int kRedBlocks = 304;  // observables partial-reduction blocks (2 x 152 SMs)
-constexpr int kTmaStages = 6;    // row-pipeline depth of the TMA-fed FP32 kernels
+constexpr int kTmaStages = LBM_TMA_STAGES;  // row-pipeline depth of the TMA-fed FP32 kernels
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
@@ -215,6 +221,13 @@ static void fill_step_params(lbmk::StepParams<real>& s, const lbm_ctx* c) {
     s.rho_split = (real)(0.5 * (c->th.rho_v + c->th.rho_l));
     const lbm_host::CS eos{p.a, p.b, p.R};
     s.mu_off_l = (real)(eos.mu((double)s.rho_ref_l, c->th.T) - eos.mu((double)s.rho_ref_v, c->th.T));
+    const double urv = 1.0 - 0.25 * p.b * (double)s.rho_ref_v, url = 1.0 - 0.25 * p.b * (double)s.rho_ref_l;
+    s.ur_v = (real)urv;
+    s.ur_l = (real)url;
+    s.ur3_v = (real)(urv * urv * urv);
+    s.ur3_l = (real)(url * url * url);
+    s.irr_v = (real)(1.0 / (double)s.rho_ref_v);
+    s.irr_l = (real)(1.0 / (double)s.rho_ref_l);
     s.s_e = (real)(1.0 / p.tau_e);
     s.s_z = (real)(1.0 / p.tau_zeta);
     s.s_q = (real)(1.0 / p.tau_q);
@@ -225,9 +238,15 @@ static void fill_step_params(lbmk::StepParams<real>& s, const lbm_ctx* c) {
 
 static int choose_rows(int nx, int ny, int tx) {
     // Enough CTAs to fill 152 SMs several times over, but long strips so the y halo
-    // (recomputed rows) stays a few percent.
+    // (recomputed rows) stays a few percent.  LBM_ROWS overrides (tuning experiments).
+    if (const char* e = std::getenv("LBM_ROWS")) {
+        const int r = std::atoi(e);
+        if (r >= 1) return r < ny ? r : ny;
+    }
+    // About 14 strips per SM: several waves of CTAs, so the last partial wave is a small
+    // fraction of the launch (measured: 32-row strips beat 64-row ones by 8-10% at 4096^2).
     const long long gx = (nx + tx - 1) / tx;
-    const long long target = 152LL * 8;
+    const long long target = 152LL * 14;
     long long rows = (ny * gx + target - 1) / target;
     if (rows < 8) rows = 8;
     if (rows > 64) rows = 64;
@@ -305,6 +324,19 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->ready = false;
     fill_step_params(c->spf, c);
     fill_step_params(c->spd, c);
+    if (c->use_tma) {
+        // the stage rings of wide tiles exceed the default 48 KB of dynamic shared memory
+        cudaError_t e1 = cudaFuncSetAttribute(lbmk::pp_step_tma<kTXf, kTmaStages>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)sizeof(lbmk::PPTmaSmem<kTXf, kTmaStages>));
+        cudaError_t e2 = cudaFuncSetAttribute(lbmk::fe_step_tma<kTXf, kTmaStages>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)sizeof(lbmk::FETmaSmem<kTXf, kTmaStages>));
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            lbm_destroy(c);
+            return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaFuncSetAttribute(max dynamic smem)");
+        }
+    }
     *out = c;
     return LBM_OK;
 }

@@ -30,16 +30,23 @@ struct StepParams {
     real kappa;        // free energy: mu = mu_b - kappa lap rho
     real rho_ref_v, rho_ref_l, rho_split;  // coexistence densities (reference points of mu_b) and midpoint
     real mu_off_l;     // mu_b(rho_ref_l) - mu_b(rho_ref_v) at the rounded references (host FP64)
+    real ur_v, ur_l;   // 1 - b rho_ref / 4 of each reference
+    real ur3_v, ur3_l; // its cube
+    real irr_v, irr_l; // 1 / rho_ref
     real s_e, s_z, s_q, s_nu;  // relaxation rates 1/tau (Eq. 3); tau_rho, tau_j drop out
     real fx, fy;       // body force
 };
 
+// Correctly rounded reciprocal (FP32: one hardware-assisted sequence instead of a full division).
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
 template <typename real>
 __device__ __forceinline__ real cs_pressure(real rho, real RT, real a, real b4) {
     const real e = b4 * rho;
-    const real om = real(1) - e;
+    const real r = rcp(real(1) - e);
     const real num = real(1) + e * (real(1) + e * (real(1) - e));
-    return rho * RT * num / (om * om * om) - a * rho * rho;
+    return rho * RT * num * (r * r * r) - a * rho * rho;
 }
 
 // Eq. (11) with G = -1: psi = sqrt(2 (rho c_s^2 - p_EOS)).  NaN for a negative radicand
@@ -62,11 +69,15 @@ template <typename real>
 __device__ __forceinline__ real mu_bulk_rel(real rho, const StepParams<real>& P) {
     const bool liq = rho >= P.rho_split;
     const real rr = liq ? P.rho_ref_l : P.rho_ref_v;
+    const real ur = liq ? P.ur_l : P.ur_v;
+    const real ur3 = liq ? P.ur3_l : P.ur3_v;
+    const real irr = liq ? P.irr_l : P.irr_v;
     const real d = rho - rr;
-    const real u = real(1) - P.b4 * rho, ur = real(1) - P.b4 * rr;
-    const real u2 = u * u, ur2 = ur * ur;
-    const real dg = P.b4 * d * (real(2) * (ur2 + ur * u + u2) / (u2 * u * ur2 * ur) + (ur + u) / (u2 * ur2));
-    return P.RT * (dg + log1p(d / rr)) - real(2) * P.a * d + (liq ? P.mu_off_l : real(0));
+    const real u = real(1) - P.b4 * rho;
+    // g(e) - g(e_r) = (e - e_r) [2 (ur^2 + ur u + u^2) + (ur + u) u ur] / (u^3 ur^3)
+    const real num = real(2) * (ur * ur + ur * u + u * u) + (ur + u) * u * ur;
+    const real dg = P.b4 * d * num * rcp(u * u * u * ur3);
+    return P.RT * (dg + log1p(d * irr)) - real(2) * P.a * d + (liq ? P.mu_off_l : real(0));
 }
 
 __device__ __forceinline__ int wrap_idx(int i, int n) {
@@ -147,7 +158,7 @@ __device__ __forceinline__ void pp_collide(real v[9], real rho, real pc, const r
     // Eq. (6b) and the moments m = M f (Eq. S48)
     const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
     const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
-    const real inv_rho = real(1) / rho;
+    const real inv_rho = rcp(rho);
     const real ux = (jx + real(0.5) * Fx) * inv_rho;
     const real uy = (jy + real(0.5) * Fy) * inv_rho;
     const real sax = (v[1] + v[2]) + (v[3] + v[4]);
@@ -191,7 +202,7 @@ __device__ __forceinline__ void fe_collide(real v[9], real rho, const real mn[9]
     const real Fx = -rho * gmx + P.fx, Fy = -rho * gmy + P.fy;
     const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
     const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
-    const real inv_rho = real(1) / rho;
+    const real inv_rho = rcp(rho);
     const real ux = (jx + real(0.5) * Fx) * inv_rho;
     const real uy = (jy + real(0.5) * Fy) * inv_rho;
     const real sax = (v[1] + v[2]) + (v[3] + v[4]);

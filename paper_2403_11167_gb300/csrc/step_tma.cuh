@@ -165,9 +165,24 @@ struct PPTmaSmem {
     uint64_t bar[S];
 };
 
+__device__ __forceinline__ int next_stage(int s, int S) { return s + 1 == S ? 0 : s + 1; }
+
 // Pseudopotential step (Eqs. 1, 4, 6, 10, 11, 13, 28, 30-32), TMA-fed.
+// Iteration q computes psi of row q (needs staged rows q-1..q+1), then, after the one
+// barrier of the row, collides row q-1.
+// Minimum resident CTAs per SM given to ptxas.  These kernels are issue-bound, and a
+// register budget beats occupancy (measured: 1 block minimum, i.e. no register cap, was
+// 10-25% faster than caps matching the shared-memory occupancy); an explicit bound also
+// keeps ptxas from trading registers for spills, which a bare thread bound provoked.
+#ifndef LBM_PP_MINB
+#define LBM_PP_MINB 1
+#endif
+#ifndef LBM_FE_MINB
+#define LBM_FE_MINB 1
+#endif
+
 template <int TX, int S>
-__global__ void __launch_bounds__(TX + 32) pp_step_tma(const float* __restrict__ fin, float* __restrict__ fout,
+__global__ void __launch_bounds__(TX + 32, LBM_PP_MINB) pp_step_tma(const float* __restrict__ fin, float* __restrict__ fout,
                                                        const StepParams<float> P, int* __restrict__ err) {
     constexpr int W8 = TX + 8;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -201,24 +216,25 @@ __global__ void __launch_bounds__(TX + 32) pp_step_tma(const float* __restrict__
     if (producer) {
         for (int k = 0; k < S && k < nsrc; ++k)
             issue_row<W8>(fin, P.pitch, nx, wrap_once(rbase + k, ny), x0, w, sm.stage[k], &sm.bar[k], err, k,
-                              sm.stage[0], sm.stage[0] + S * 9 * W8);
+                          sm.stage[0], sm.stage[0] + S * 9 * W8);
         issued = min(S, nsrc);
     }
     float prv[9], cur[9];
+    float rho_prv = 1.0f, rho_cur = 1.0f;
     // The first iteration reads the stages of rows y0-2 and y0-1 (fills 0 and 1) besides the
     // one it waits for; wait for those two here, so every fill is waited on before it is read
     // and before its stage is re-armed for the next fill.
     bool failed = __syncthreads_or(!(mbar_wait_bounded(&sm.bar[0], 0) && mbar_wait_bounded(&sm.bar[1], 0)));
+    int sm2 = 0, sm1 = 1, s0 = 2 % S;  // stages of rows q-1, q, q+1
+    uint32_t par = 0;                  // parity of the fill being waited for (stage s0)
 #pragma unroll 1
     for (int q = y0 - 1; q <= y1 && !failed; ++q) {
         const int k = q + 1 - rbase;  // staged index of row q+1
-        const bool ok = mbar_wait_bounded(&sm.bar[k % S], (uint32_t)((k / S) & 1));
+        const bool ok = mbar_wait_bounded(&sm.bar[s0], par);
         if (ok && has_col) {
-            const float* Rm = sm.stage[(k - 2) % S];
-            const float* R0 = sm.stage[(k - 1) % S];
-            const float* Rp = sm.stage[k % S];
-            pull_smem<W8>(Rm, R0, Rp, sc, cur);
-            sm.psi[q & 3][col + 1] = pseudo_psi(sum9(cur), P);
+            pull_smem<W8>(sm.stage[sm2], sm.stage[sm1], sm.stage[s0], sc, cur);
+            rho_cur = sum9(cur);
+            sm.psi[q & 3][col + 1] = pseudo_psi(rho_cur, P);
         }
         if (__syncthreads_or(!ok)) {
 #ifdef LBM_TMA_CHECKS
@@ -235,7 +251,7 @@ __global__ void __launch_bounds__(TX + 32) pp_step_tma(const float* __restrict__
         if (producer && k - 2 + S < nsrc) {
             fence_proxy_async_smem();
             const int kk = k - 2 + S;
-            issue_row<W8>(fin, P.pitch, nx, wrap_once(rbase + kk, ny), x0, w, sm.stage[kk % S], &sm.bar[kk % S], err,
+            issue_row<W8>(fin, P.pitch, nx, wrap_once(rbase + kk, ny), x0, w, sm.stage[sm2], &sm.bar[sm2], err,
                           kk, sm.stage[0], sm.stage[0] + S * 9 * W8);
             issued = kk + 1;
         }
@@ -254,13 +270,18 @@ __global__ void __launch_bounds__(TX + 32) pp_step_tma(const float* __restrict__
             pn[6] = pp[c1 - 1];
             pn[7] = pm[c1 - 1];
             pn[8] = pm[c1 + 1];
-            pp_collide(prv, sum9(prv), pn[0], pn, P);
+            pp_collide(prv, rho_prv, pn[0], pn, P);
             float* o = fout + (long long)(q - 1) * nx + x0 + col;
 #pragma unroll
             for (int i = 0; i < 9; ++i) o[i * P.pitch] = prv[i];
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) prv[i] = cur[i];
+        rho_prv = rho_cur;
+        sm2 = sm1;
+        sm1 = s0;
+        s0 = next_stage(s0, S);
+        if (s0 == 0) par ^= 1u;
     }
     if (failed && producer) {
         atomicExch(err, 1);
@@ -277,9 +298,11 @@ struct FETmaSmem {
     uint64_t bar[S];
 };
 
-// Free-energy step (Eqs. 1, 6, 20, 21, 24, 29), TMA-fed.
+// Free-energy step (Eqs. 1, 6, 20, 21, 24, 29), TMA-fed, one barrier per row:
+// iteration q computes rho of row q and mu of row q-2 (whose rho rows q-3..q-1 were
+// written in earlier iterations), then, after the barrier, collides row q-3.
 template <int TX, int S>
-__global__ void __launch_bounds__(TX + 32) fe_step_tma(const float* __restrict__ fin, float* __restrict__ fout,
+__global__ void __launch_bounds__(TX + 32, LBM_FE_MINB) fe_step_tma(const float* __restrict__ fin, float* __restrict__ fout,
                                                        const StepParams<float> P, int* __restrict__ err) {
     constexpr int W8 = TX + 8;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -306,7 +329,7 @@ __global__ void __launch_bounds__(TX + 32) fe_step_tma(const float* __restrict__
     }
     const int sc = col + 4, rc = col + 2, mc = col + 1;
     const int rbase = y0 - 3;
-    const int nsrc = y1 + 2 - rbase + 1;  // source rows y0-3 .. y1+2
+    const int nsrc = y1 + 2 - rbase + 1;  // source rows y0-3 .. y1+2 (rho rows y0-2 .. y1+1)
     if (producer) {
         for (int s = 0; s < S; ++s) mbar_init(&sm.bar[s], 1);
         fence_mbar_init();
@@ -316,44 +339,32 @@ __global__ void __launch_bounds__(TX + 32) fe_step_tma(const float* __restrict__
     if (producer) {
         for (int k = 0; k < S && k < nsrc; ++k)
             issue_row<W8>(fin, P.pitch, nx, wrap_once(rbase + k, ny), x0, w, sm.stage[k], &sm.bar[k], err, k,
-                              sm.stage[0], sm.stage[0] + S * 9 * W8);
+                          sm.stage[0], sm.stage[0] + S * 9 * W8);
         issued = min(S, nsrc);
     }
-    float p2[9], p1[9], cur[9];  // pulled populations of rows q-2, q-1, q
+    float p3[9], p2[9], p1[9], cur[9];  // pulled populations of rows q-3, q-2, q-1, q
     // wait for fills 0 and 1 (rows y0-3, y0-2), read by the first iteration besides the one
     // it waits for (see pp_step_tma)
     bool failed = __syncthreads_or(!(mbar_wait_bounded(&sm.bar[0], 0) && mbar_wait_bounded(&sm.bar[1], 0)));
+    int sm2 = 0, sm1 = 1, s0 = 2 % S;
+    uint32_t par = 0;
 #pragma unroll 1
-    for (int q = y0 - 2; q <= y1 + 1 && !failed; ++q) {
+    for (int q = y0 - 2; q <= y1 + 2 && !failed; ++q) {
         const int k = q + 1 - rbase;
-        const bool ok = mbar_wait_bounded(&sm.bar[k % S], (uint32_t)((k / S) & 1));
-        if (ok && has_col) {
-            pull_smem<W8>(sm.stage[(k - 2) % S], sm.stage[(k - 1) % S], sm.stage[k % S], sc, cur);
-            sm.rho[q & 7][rc] = sum9(cur);
-        }
-        if (__syncthreads_or(!ok)) {
-#ifdef LBM_TMA_CHECKS
-            if (!ok && atomicCAS(err + 8, 0, 1) == 0) {
-                err[9] = (int)blockIdx.x;
-                err[10] = (int)blockIdx.y;
-                err[11] = q;
-                err[12] = k;
+        const bool load = q <= y1 + 1;  // rho rows run to y1+1; the last iteration only finishes mu and collides
+        bool ok = true;
+        if (load) {
+            ok = mbar_wait_bounded(&sm.bar[s0], par);
+            if (ok && has_col) {
+                pull_smem<W8>(sm.stage[sm2], sm.stage[sm1], sm.stage[s0], sc, cur);
+                sm.rho[q & 7][rc] = sum9(cur);
             }
-#endif
-            failed = true;
-            break;
         }
-        if (producer && k - 2 + S < nsrc) {
-            fence_proxy_async_smem();
-            const int kk = k - 2 + S;
-            issue_row<W8>(fin, P.pitch, nx, wrap_once(rbase + kk, ny), x0, w, sm.stage[kk % S], &sm.bar[kk % S], err,
-                          kk, sm.stage[0], sm.stage[0] + S * 9 * W8);
-            issued = kk + 1;
-        }
-        if (has_mu && q >= y0) {
-            const float* rm = sm.rho[(q - 2) & 7];
-            const float* r0 = sm.rho[(q - 1) & 7];
-            const float* rp = sm.rho[q & 7];
+        if (has_mu && q >= y0 + 1) {
+            // mu of row q-2 from rho rows q-3, q-2, q-1 (written before the previous barrier)
+            const float* rm = sm.rho[(q - 3) & 7];
+            const float* r0 = sm.rho[(q - 2) & 7];
+            const float* rp = sm.rho[(q - 1) & 7];
             float rn[9];
             rn[1] = r0[rc + 1];
             rn[2] = rp[rc];
@@ -363,30 +374,48 @@ __global__ void __launch_bounds__(TX + 32) fe_step_tma(const float* __restrict__
             rn[6] = rp[rc - 1];
             rn[7] = rm[rc - 1];
             rn[8] = rm[rc + 1];
-            sm.mu[(q - 1) & 3][mc] = fe_mu(r0[rc], rn, P);
+            sm.mu[(q - 2) & 3][mc] = fe_mu(r0[rc], rn, P);
         }
-        __syncthreads();
-        if (is_main && has_col && q >= y0 + 2) {
-            const float* mm = sm.mu[(q - 3) & 3];
-            const float* m0 = sm.mu[(q - 2) & 3];
-            const float* mp = sm.mu[(q - 1) & 3];
-            const float* rm = sm.rho[(q - 3) & 7];
-            const float* r0 = sm.rho[(q - 2) & 7];
-            const float* rp = sm.rho[(q - 1) & 7];
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (producer && load && k - 2 + S < nsrc) {
+            fence_proxy_async_smem();
+            const int kk = k - 2 + S;
+            issue_row<W8>(fin, P.pitch, nx, wrap_once(rbase + kk, ny), x0, w, sm.stage[sm2], &sm.bar[sm2], err,
+                          kk, sm.stage[0], sm.stage[0] + S * 9 * W8);
+            issued = kk + 1;
+        }
+        if (is_main && has_col && q >= y0 + 3) {
+            // collide row c = q - 3: mu rows c-1..c+1 = q-4..q-2, rho rows q-4..q-2
+            const float* mm = sm.mu[(q - 4) & 3];
+            const float* m0 = sm.mu[(q - 3) & 3];
+            const float* mp = sm.mu[(q - 2) & 3];
+            const float* rm = sm.rho[(q - 4) & 7];
+            const float* r0 = sm.rho[(q - 3) & 7];
+            const float* rp = sm.rho[(q - 2) & 7];
             float mn[9], rn[9];
             mn[1] = m0[mc + 1]; mn[2] = mp[mc]; mn[3] = m0[mc - 1]; mn[4] = mm[mc];
             mn[5] = mp[mc + 1]; mn[6] = mp[mc - 1]; mn[7] = mm[mc - 1]; mn[8] = mm[mc + 1];
             rn[1] = r0[rc + 1]; rn[2] = rp[rc]; rn[3] = r0[rc - 1]; rn[4] = rm[rc];
             rn[5] = rp[rc + 1]; rn[6] = rp[rc - 1]; rn[7] = rm[rc - 1]; rn[8] = rm[rc + 1];
-            fe_collide(p2, r0[rc], mn, rn, P);
-            float* o = fout + (long long)(q - 2) * nx + x0 + col;
+            fe_collide(p3, r0[rc], mn, rn, P);
+            float* o = fout + (long long)(q - 3) * nx + x0 + col;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) o[i * P.pitch] = p2[i];
+            for (int i = 0; i < 9; ++i) o[i * P.pitch] = p3[i];
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
+            p3[i] = p2[i];
             p2[i] = p1[i];
             p1[i] = cur[i];
+        }
+        if (load) {
+            sm2 = sm1;
+            sm1 = s0;
+            s0 = next_stage(s0, S);
+            if (s0 == 0) par ^= 1u;
         }
     }
     if (failed && producer) {
