@@ -210,6 +210,57 @@ int lbm_observables_fields_static(int precision, const void* rho, const void* ux
                                   int ny, int geometry, double a, double b, double R, double T, int nblocks,
                                   double* out_dev, void* stream);
 
+/* ---------------------------------------------------------------------------------- */
+/* Batched calibration sweep (pseudopotential model, FP32).                             */
+/* The paper tunes sigma_Li, kappa_P and kappa_Li against coexistence densities, width  */
+/* and surface tension (Sec. 3, App. B) and notes that the pseudopotential model needs  */
+/* previous simulations to fix its parameters (Sec. 5.1-5.2).  A batch runs many such   */
+/* independent lattices at once on one GPU.                                             */
+
+typedef struct {
+    int nx, ny;          /* lattice size (periodic); nx % 4 == 0 unless the lattice is resident */
+    int geometry;        /* lbm_geometry used by lbm_batch_observables */
+    int pad_;
+    long long nsteps;    /* time steps of this lattice, 0 .. 2^30 */
+    lbm_params params;   /* model LBM_PSEUDOPOTENTIAL, precision LBM_F32; resolved as lbm_create */
+} lbm_batch_lattice;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Create a batch of n lattices.  rho0[i]: host array of nx*ny densities of lattice i
+ * (copied; f starts at f^eq(rho0, u = 0)).  Lattices whose populations, psi and rho fit in
+ * one CTA's shared memory (11 nx ny floats <= 200 KB, up to 4654 cells) run resident: one CTA
+ * each, all steps in shared memory, in one persistent launch.  The others run as strips
+ * of a work table, one launch per step for all of them, replayed as 64-step CUDA graphs on
+ * a second stream concurrently.  An autotuner picks the resident block size and the strip
+ * height by timing short trials (cached per shape class); the state is re-initialised
+ * afterwards.  The library allocates the device memory (one pooled cudaMalloc).
+ * Errors: LBM_ERR_ARG (sizes, densities), LBM_ERR_UNSUPPORTED (other model or precision,
+ * a tiled lattice with nx % 4 != 0 or nx < 8 or ny < 4), LBM_ERR_CUDA. */
+int lbm_batch_create(int n, const lbm_batch_lattice* lattices, const double* const* rho0, lbm_batch** out);
+
+/* Enqueue the whole sweep (every lattice its own nsteps); asynchronous.  A second call
+ * starts again from rho0. */
+int lbm_batch_run(lbm_batch* b);
+
+/* Observables of every lattice's final state (definitions of lbm_observables) into
+ * out[0..n-1]; synchronises.  LBM_ERR_STATE before lbm_batch_run. */
+int lbm_batch_observables(lbm_batch* b, lbm_obs* out);
+
+/* Final populations of lattice i (host FP64, [9][ny][nx], Eq. 2 order, post-streaming). */
+int lbm_batch_populations(lbm_batch* b, int i, double* f);
+
+/* Autotuner decisions: resident lattices, tiled work items, resident threads, strip rows. */
+int lbm_batch_info(const lbm_batch* b, int* n_resident, int* n_items, int* resident_threads, int* strip_rows);
+
+/* The stream the batch completes on (cudaStream_t). */
+void* lbm_batch_stream(const lbm_batch* b);
+
+void lbm_batch_destroy(lbm_batch* b);
+
+/* Text of the last CUDA failure of a batch call on this host thread. */
+const char* lbm_batch_last_error(void);
+
 /* Checkpoint: write/read the populations, step counter and parameters (binary). */
 int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);

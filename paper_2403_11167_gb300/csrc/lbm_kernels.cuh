@@ -439,7 +439,24 @@ __device__ __forceinline__ long long shifted_cell(int x, int y, int cx, int cy, 
     return (long long)ys * nx + xs;
 }
 
-// Pulled populations of cell (x, y): v_i = S_i(x - c_i) = f_i(x).
+// Pulled populations of cell (x, y) from populations in shared memory (plain loads; the
+// read-only global path of pull9 must not be given a shared-memory address).
+template <typename real>
+__device__ __forceinline__ void pull_cell_shared(const real* S, int N, int x, int y, int nx, int ny, real v[9]) {
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int om = (y == 0 ? ny - 1 : y - 1) * nx, o0 = y * nx, op = (y == ny - 1 ? 0 : y + 1) * nx;
+    v[0] = S[0 * N + o0 + x];
+    v[1] = S[1 * N + o0 + xm];
+    v[2] = S[2 * N + om + x];
+    v[3] = S[3 * N + o0 + xp];
+    v[4] = S[4 * N + op + x];
+    v[5] = S[5 * N + om + xm];
+    v[6] = S[6 * N + om + xp];
+    v[7] = S[7 * N + op + xp];
+    v[8] = S[8 * N + op + xm];
+}
+
+// Pulled populations of cell (x, y) from global memory: v_i = S_i(x - c_i) = f_i(x).
 template <typename real>
 __device__ __forceinline__ void pull_cell(const real* __restrict__ S, long long pitch, int x, int y, int nx, int ny,
                                           real v[9]) {

@@ -181,17 +181,13 @@ __device__ __forceinline__ int next_stage(int s, int S) { return s + 1 == S ? 0 
 #define LBM_FE_MINB 1
 #endif
 
+// One CTA's strip of the pseudopotential step: columns [x0, x0 + w), rows [y0, y1).
 template <int TX, int S>
-__global__ void __launch_bounds__(TX + 32, LBM_PP_MINB) pp_step_tma(const float* __restrict__ fin, float* __restrict__ fout,
-                                                       const StepParams<float> P, int* __restrict__ err) {
+__device__ __forceinline__ void pp_strip_tma(const float* __restrict__ fin, float* __restrict__ fout,
+                                             const StepParams<float>& P, int x0, int w, int y0, int y1,
+                                             PPTmaSmem<TX, S>& sm, int* __restrict__ err) {
     constexpr int W8 = TX + 8;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    PPTmaSmem<TX, S>& sm = *reinterpret_cast<PPTmaSmem<TX, S>*>(smem_raw);
     const int nx = P.nx, ny = P.ny;
-    const int x0 = blockIdx.x * TX;
-    const int w = min(TX, nx - x0);
-    const int y0 = blockIdx.y * P.rows;
-    const int y1 = min(y0 + P.rows, ny);
     const int t = threadIdx.x;
     const bool is_main = t < TX;
     const bool producer = t == TX;
@@ -287,6 +283,16 @@ __global__ void __launch_bounds__(TX + 32, LBM_PP_MINB) pp_step_tma(const float*
         atomicExch(err, 1);
         drain_stages<S>(sm.bar, issued);
     }
+}
+
+template <int TX, int S>
+__global__ void __launch_bounds__(TX + 32, LBM_PP_MINB) pp_step_tma(const float* __restrict__ fin, float* __restrict__ fout,
+                                                       const StepParams<float> P, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    PPTmaSmem<TX, S>& sm = *reinterpret_cast<PPTmaSmem<TX, S>*>(smem_raw);
+    const int x0 = blockIdx.x * TX;
+    const int y0 = blockIdx.y * P.rows;
+    pp_strip_tma<TX, S>(fin, fout, P, x0, min(TX, P.nx - x0), y0, min(y0 + P.rows, P.ny), sm, err);
 }
 
 template <int TX, int S>

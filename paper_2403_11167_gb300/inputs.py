@@ -38,3 +38,40 @@ def spinodal_noise(nx: int, ny: int, rho_mean: float, amp: float = 0.01, seed: i
 def random_field(nx: int, ny: int, lo: float, hi: float, seed: int = 0) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(lo, hi, size=(ny, nx))
+
+
+def calibration_sweep(n: int = 512, seed: int = 11167, step_range=(5000, 20000), w0: float = 5.0):
+    """Seeded parameter sets of a pseudopotential calibration sweep (uneven lattices).
+
+    Half flat slabs (nx in {64, 128, 256, 512}, ny = 4), half centred droplets on L x L
+    lattices (L in {64, 128, 192, 256, 384, 512}, radius R ~ U[10, 80] redrawn until
+    L >= 2R + 8 w0).  Tr ~ U[0.5, 0.95], width factor kappa_P in {0.4, 0.7, 1.0},
+    tau ~ U[0.6, 1.2], steps ~ U{step_range}, a = 0.25, b = 4, R = 1.  Returns a list of
+    dicts; the caller builds each initial density from the lattice's Maxwell densities
+    with ``flat_slab`` / ``droplet``.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        flat = i % 2 == 0
+        d = dict(a=0.25, Tr=float(rng.uniform(0.5, 0.95)), kappa_P=float(rng.choice([0.4, 0.7, 1.0])),
+                 tau=float(rng.uniform(0.6, 1.2)),
+                 nsteps=int(rng.integers(step_range[0], step_range[1] + 1)))
+        if flat:
+            d.update(geometry=0, nx=int(rng.choice([64, 128, 256, 512])), ny=4, radius=0.0)
+        else:
+            L = int(rng.choice([64, 128, 192, 256, 384, 512]))
+            while True:
+                R = float(rng.uniform(10.0, 80.0))
+                if L >= 2 * R + 8 * w0:
+                    break
+            d.update(geometry=1, nx=L, ny=L, radius=R)
+        out.append(d)
+    return out
+
+
+def sweep_density(spec: dict, rho_v: float, rho_l: float, w0: float = 5.0) -> np.ndarray:
+    """Initial density of one sweep lattice (flat slab or droplet) from its bulk densities."""
+    if spec["geometry"] == 0:
+        return flat_slab(spec["nx"], spec["ny"], rho_v, rho_l, w0)
+    return droplet(spec["nx"], spec["ny"], spec["radius"], rho_v, rho_l, w0)

@@ -56,6 +56,10 @@ class lbm_thermo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lbm_batch_lattice(ctypes.Structure):
+    pass
+
+
 class lbm_obs(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("rho_l", "rho_v", "width", "dp", "u_max", "mass", "radius")] + [
         ("step", ctypes.c_longlong), ("status", ctypes.c_int), ("pad_", ctypes.c_int)]
@@ -64,12 +68,16 @@ class lbm_obs(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
+lbm_batch_lattice._fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("geometry", ctypes.c_int),
+                              ("pad_", ctypes.c_int), ("nsteps", ctypes.c_longlong), ("params", lbm_params)]
+
+
 class LBMError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
         msg = f"{what}: {lbm_strerror(code)} ({code})"
         if code == LBM_ERR_CUDA:
-            msg += " -- " + _lib().lbm_last_cuda_error().decode()
+            msg += " -- " + _lib().lbm_last_cuda_error().decode() + " " + _lib().lbm_batch_last_error().decode()
         super().__init__(msg)
 
 
@@ -112,6 +120,15 @@ def _lib():
             "lbm_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "lbm_build_info": ([], ctypes.c_char_p),
             "lbm_last_cuda_error": ([], ctypes.c_char_p),
+            "lbm_batch_create": ([ctypes.c_int, ctypes.POINTER(lbm_batch_lattice),
+                                  ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(vp)], ctypes.c_int),
+            "lbm_batch_run": ([vp], ctypes.c_int),
+            "lbm_batch_observables": ([vp, O], ctypes.c_int),
+            "lbm_batch_populations": ([vp, ctypes.c_int, dp], ctypes.c_int),
+            "lbm_batch_info": ([vp] + [ctypes.POINTER(ctypes.c_int)] * 4, ctypes.c_int),
+            "lbm_batch_stream": ([vp], vp),
+            "lbm_batch_destroy": ([vp], None),
+            "lbm_batch_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -274,5 +291,75 @@ class Context:
         self.stream.synchronize()
 
 
-def nan():
-    return math.nan
+class Batch:
+    """Owner of one ``lbm_batch`` (batched pseudopotential calibration sweep)."""
+
+    def __init__(self, specs, rho0s):
+        n = len(specs)
+        arr = (lbm_batch_lattice * n)()
+        self._keep = []
+        ptrs = (ctypes.POINTER(ctypes.c_double) * n)()
+        self.shapes = []
+        for i, (s, r) in enumerate(zip(specs, rho0s)):
+            arr[i].nx, arr[i].ny, arr[i].geometry = s["nx"], s["ny"], s["geometry"]
+            arr[i].nsteps = s["nsteps"]
+            arr[i].params = s["params"]
+            r = np.ascontiguousarray(r, dtype=np.float64)
+            assert r.shape == (s["ny"], s["nx"])
+            self._keep.append(r)
+            ptrs[i] = _dptr(r)
+            self.shapes.append((s["ny"], s["nx"]))
+        h = ctypes.c_void_p()
+        _check(_lib().lbm_batch_create(n, arr, ptrs, ctypes.byref(h)), "lbm_batch_create")
+        self.h = h
+        self.n = n
+
+    def run(self):
+        _check(_lib().lbm_batch_run(self.h), "lbm_batch_run")
+
+    def observables(self):
+        out = (lbm_obs * self.n)()
+        _check(_lib().lbm_batch_observables(self.h, out), "lbm_batch_observables")
+        return [o.as_dict() for o in out]
+
+    def populations(self, i):
+        ny, nx = self.shapes[i]
+        f = np.zeros((9, ny, nx))
+        _check(_lib().lbm_batch_populations(self.h, i, _dptr(f)), "lbm_batch_populations")
+        return f
+
+    def info(self):
+        vals = [ctypes.c_int() for _ in range(4)]
+        _check(_lib().lbm_batch_info(self.h, *[ctypes.byref(v) for v in vals]), "lbm_batch_info")
+        return dict(zip(("n_resident", "n_items", "resident_threads", "strip_rows"), [v.value for v in vals]))
+
+    def synchronize(self):
+        import torch
+
+        torch.cuda.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sweep_specs(entries, precision=LBM_F32):
+    """lbm_batch_lattice-ready dicts (with resolved Maxwell densities) from
+    ``inputs.calibration_sweep`` entries; the initial densities come from ``inputs``."""
+    from . import inputs
+
+    specs, rhos = [], []
+    for e in entries:
+        p = lbm_params_default(LBM_PSEUDOPOTENTIAL, precision=precision, a=e["a"], Tr=e["Tr"], tau_nu=e["tau"],
+                               kappa_P=e["kappa_P"])
+        _, th = lbm_resolve_params(p)
+        specs.append(dict(nx=e["nx"], ny=e["ny"], geometry=e["geometry"], nsteps=e["nsteps"], params=p))
+        rhos.append(inputs.sweep_density(e, th.rho_v, th.rho_l))
+    return specs, rhos

@@ -1,0 +1,113 @@
+"""Batched calibration sweep (one persistent resident launch + work-table strip kernel)
+against single-lattice runs through the plain API and against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import observables as OO
+from paper_2403_11167_gb300 import inputs
+from helpers import max_rel, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2403_11167_gb300 import lbm as L
+
+    return L
+
+
+def _small_sweep(n, seed, steps):
+    return inputs.calibration_sweep(n, seed=seed, step_range=steps)
+
+
+def test_batch_equals_single_lattice_runs(lbm):
+    """Every lattice of a mixed batch (resident slabs and 64^2 droplets, tiled droplets up to
+    512^2, uneven step counts) ends in exactly the state the plain single-lattice path reaches:
+    the same per-cell arithmetic runs in the resident kernel, the work-table strip kernel and
+    the single-lattice kernels.  Parameter draws outside the model's stable range (e.g. low Tr
+    with a thin interface) diverge identically on both paths and are reported as diverged."""
+    entries = _small_sweep(20, seed=5, steps=(60, 300))
+    specs, rhos = lbm.sweep_specs(entries)
+    b = lbm.Batch(specs, rhos)
+    info = b.info()
+    assert info["n_resident"] > 0 and info["n_items"] > 0
+    b.run()
+    obs = b.observables()
+    diverged = 0
+    for i, (s, r) in enumerate(zip(specs, rhos)):
+        ctx = lbm.Context(s["params"], s["nx"], s["ny"])
+        ctx.set_density(r)
+        ctx.step(s["nsteps"])
+        fb, fc = b.populations(i), ctx.populations()
+        assert np.array_equal(fb, fc, equal_nan=True), (i, s["nx"], s["ny"], np.nanmax(np.abs(fb - fc)))
+        oc = ctx.observables(s["geometry"])
+        assert obs[i]["status"] == oc["status"], i
+        if oc["status"] == 0:
+            for k in ("rho_l", "rho_v", "width", "dp", "mass"):
+                assert abs(obs[i][k] - oc[k]) <= 1e-12 * max(1.0, abs(oc[k])), (i, k)
+        else:
+            diverged += 1
+        ctx.close()
+    assert diverged < len(specs) // 2
+    b.close()
+
+
+def test_batch_rerun_is_reproducible(lbm):
+    entries = _small_sweep(8, seed=9, steps=(50, 120))
+    specs, rhos = lbm.sweep_specs(entries)
+    b = lbm.Batch(specs, rhos)
+    b.run()
+    first = [b.populations(i) for i in range(len(specs))]
+    b.run()
+    for i in range(len(specs)):
+        assert np.array_equal(first[i], b.populations(i), equal_nan=True)
+    b.close()
+
+
+def test_batch_vs_oracle(lbm):
+    """FP32 batch against the FP64 oracle: resident slabs for 2000 steps, a resident 64^2
+    droplet for 1000 steps and a tiled 128^2 droplet for 300 steps; max relative density
+    error <= 1e-5, observables of the oracle fields within 1e-5."""
+    base = dict(a=0.25, kappa_P=0.7, tau=0.9)
+    entries = [
+        dict(base, Tr=0.8, geometry=0, nx=64, ny=4, radius=0.0, nsteps=2000),
+        dict(base, Tr=0.6, geometry=0, nx=128, ny=4, radius=0.0, nsteps=2000),
+        dict(base, Tr=0.9, geometry=1, nx=64, ny=64, radius=15.0, nsteps=1000),
+        dict(base, Tr=0.75, geometry=1, nx=128, ny=128, radius=30.0, nsteps=300),
+    ]
+    specs, rhos = lbm.sweep_specs(entries)
+    b = lbm.Batch(specs, rhos)
+    b.run()
+    obs = b.observables()
+    for i, (s, r) in enumerate(zip(specs, rhos)):
+        rp, th = lbm.lbm_resolve_params(s["params"])
+        op = oracle_params(rp, th)
+        f_ref = O.run(O.PP, op, O.init(O.PP, r), s["nsteps"])
+        rho_ref, ux_ref, uy_ref, *_ = O.macro(O.PP, op, f_ref)
+        assert max_rel(b.populations(i).sum(0), rho_ref) < 1e-5, i
+        ref = OO.observables(rho_ref, ux_ref, uy_ref, s["geometry"], rp.a, rp.b, rp.R, th.T)
+        for k in ("rho_l", "rho_v", "mass"):
+            assert abs(obs[i][k] / ref[k] - 1) < 1e-5, (i, k)
+    b.close()
+
+
+def test_batch_argument_errors(lbm):
+    rho = np.full((4, 64), 0.1)
+    p = lbm.lbm_params_default(lbm.LBM_FREE_ENERGY)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Batch([dict(nx=64, ny=4, geometry=0, nsteps=10, params=p)], [rho])
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+    p = lbm.lbm_params_default(lbm.LBM_PSEUDOPOTENTIAL)
+    big = np.full((130, 130), 0.1)  # too large to be resident, nx % 4 != 0: not tileable
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Batch([dict(nx=130, ny=130, geometry=1, nsteps=10, params=p)], [big])
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+    bad = np.full((4, 64), -0.1)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Batch([dict(nx=64, ny=4, geometry=0, nsteps=10, params=p)], [bad])
+    assert e.value.code == lbm.LBM_ERR_ARG
