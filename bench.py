@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched-vs-plain calibration sweep")
+    ap.add_argument("--sweep-lattices", type=int, default=512)
     return ap.parse_args()
 
 
@@ -172,6 +174,50 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def run_sweep(args):
+    """Calibration sweep of 512 seeded pseudopotential lattices (uneven sizes 64x4 .. 512x512,
+    flat slabs and droplets, Tr ~ U[0.5, 0.95], kappa_P in {0.4, 0.7, 1}, tau ~ U[0.6, 1.2],
+    5e3 .. 2e4 steps), FP32: runs/s of one batched sweep (lbm_batch_run + observables) against
+    the same lattices solved one at a time through the single-lattice API (set_density +
+    step + observables on pre-created contexts).  Allocation and autotuning are outside both
+    timed regions."""
+    import torch
+
+    from paper_2403_11167_gb300 import inputs, lbm
+
+    entries = inputs.calibration_sweep(args.sweep_lattices, seed=11167)
+    specs, rhos = lbm.sweep_specs(entries)
+    cells = sum(s["nx"] * s["ny"] * s["nsteps"] for s in specs)
+    b = lbm.Batch(specs, rhos)
+    info = b.info()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    b.run()
+    obs = b.observables()
+    t_batch = time.perf_counter() - t
+    diverged = sum(1 for o in obs if o["status"] != 0)
+    b.close()
+    ctxs = [lbm.Context(s["params"], s["nx"], s["ny"]) for s in specs]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for ctx, s, r in zip(ctxs, specs, rhos):
+        ctx.set_density(r)
+        ctx.step(s["nsteps"])
+        ctx.observables(s["geometry"])
+    t_plain = time.perf_counter() - t
+    for ctx in ctxs:
+        ctx.close()
+    n = len(specs)
+    return {"lattices": n, "cell_updates": cells, "batched_s": t_batch, "plain_s": t_plain,
+            "batched_runs_per_s": n / t_batch, "plain_runs_per_s": n / t_plain, "speedup": t_plain / t_batch,
+            "batched_mlups": cells / t_batch / 1e6, "plain_mlups": cells / t_plain / 1e6,
+            "diverged_lattices": diverged, "resident_lattices": info["n_resident"],
+            "tiled_work_items": info["n_items"], "resident_threads": info["resident_threads"],
+            "strip_rows": info["strip_rows"],
+            "workload": "512 seeded pseudopotential calibration lattices (64x4..512x512 slabs and droplets, "
+                        "5e3-2e4 steps), FP32"}
 
 
 def kernel_source_hash():
@@ -311,6 +357,9 @@ def run_ours(args):
         per_model[key] = {"mlups": ncell / per_launch_s[m] / 1e6, "us_per_launch": per_launch_s[m] * 1e6,
                           "gbs_at_72B": BYTES_PER_CELL_F32 * ncell / per_launch_s[m] / 1e9,
                           "frac_of_hbm": BYTES_PER_CELL_F32 * ncell / per_launch_s[m] / 1e9 / peak}
+    sweep = None
+    if not args.no_sweep:
+        sweep = run_sweep(args)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         v, cores, sample = oracle_mlups(rho0, args.cpu_seconds)
@@ -321,6 +370,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": args.steps * (2 + 2 * nsteps), "clocks": clocks, "per_model": per_model,
+        "sweep": sweep,
         "kernel_source_sha256_12": kernel_source_hash(),
     }
     print(json.dumps(line))

@@ -127,16 +127,22 @@ static double simpson(F f, double lo, double hi, int n) {
 int li_epsilon(const CS& eos, double T, double rv, double rl, double p0, double* eps_out) {
     // F(eps)  = int (p - p0) psi' / psi^(1+eps) d rho                  (Eq. S13)
     // F'(eps) = -int (p - p0) psi' ln(psi) / psi^(1+eps) d rho          (d/d eps of S13)
+    // Newton at a given panel count, started from *eps (2 on the first level, the previous
+    // level's root afterwards: one or two steps suffice once the rule is fine enough).
     auto solve = [&](int n, double* eps) {
-        double e = 2.0;  // initial guess of Appendix B
+        double e = *eps;
         for (int it = 0; it < 100; ++it) {
-            const double F = simpson([&](double r) {
-                return (eos.p(r, T) - p0) * dpsi_of(eos, r, T) / std::pow(psi_of(eos, r, T), 1.0 + e);
-            }, rv, rl, n);
-            const double dF = simpson([&](double r) {
+            // Simpson's rule in s = ln(rho) (d rho = rho ds): the integrand varies sharply near
+            // the small vapour density in rho but smoothly in ln(rho).
+            const double F = simpson([&](double s) {
+                const double r = std::exp(s);
+                return r * (eos.p(r, T) - p0) * dpsi_of(eos, r, T) / std::pow(psi_of(eos, r, T), 1.0 + e);
+            }, std::log(rv), std::log(rl), n);
+            const double dF = simpson([&](double s) {
+                const double r = std::exp(s);
                 const double ps = psi_of(eos, r, T);
-                return -(eos.p(r, T) - p0) * dpsi_of(eos, r, T) * std::log(ps) / std::pow(ps, 1.0 + e);
-            }, rv, rl, n);
+                return -r * (eos.p(r, T) - p0) * dpsi_of(eos, r, T) * std::log(ps) / std::pow(ps, 1.0 + e);
+            }, std::log(rv), std::log(rl), n);
             if (!(std::isfinite(F) && std::isfinite(dF)) || dF == 0.0) return false;
             const double step = -F / dF;
             e += step;
@@ -145,13 +151,14 @@ int li_epsilon(const CS& eos, double T, double rv, double rl, double p0, double*
         *eps = e;
         return std::isfinite(e);
     };
-    double e0, e1;
-    int n = 2048;
+    double e0 = 2.0;  // initial guess of Appendix B
+    int n = 256;
     if (!solve(n, &e0)) return LBM_ERR_NOCONVERGE;
+    double e1 = e0;
     for (;;) {
         n *= 2;
         if (!solve(n, &e1)) return LBM_ERR_NOCONVERGE;
-        if (std::fabs(e1 - e0) < 1e-13 || n >= (1 << 20)) break;
+        if (std::fabs(e1 - e0) < 1e-12 || n >= (1 << 20)) break;
         e0 = e1;
     }
     *eps_out = e1;
