@@ -121,6 +121,12 @@ int lbm_params_default(int model, lbm_params* p);
  * LBM_ERR_NOCONVERGE if a solve fails, LBM_ERR_UNSUPPORTED for A != 0. */
 int lbm_resolve_params(const lbm_params* in, lbm_params* out, lbm_thermo* th);
 
+/* Host-only: lbm_resolve_params on each of in[0..n-1], spread over the host's cores
+ * (std::thread); identical inputs are resolved once.  status[i] receives each item's
+ * return code (out[i], th[i] are valid where it is LBM_OK).  Returns LBM_ERR_ARG for
+ * n < 0 or NULL arrays with n > 0, else LBM_OK. */
+int lbm_resolve_params_many(int n, const lbm_params* in, lbm_params* out, lbm_thermo* th, int* status);
+
 /* Bytes of device workspace a context of this size and precision needs. */
 size_t lbm_workspace_bytes(int precision, int nx, int ny);
 
@@ -260,6 +266,62 @@ void lbm_batch_destroy(lbm_batch* b);
 
 /* Text of the last CUDA failure of a batch call on this host thread. */
 const char* lbm_batch_last_error(void);
+
+/* ---------------------------------------------------------------------------------- */
+/* Learned calibration surrogate of the pseudopotential model (the paper has no network; */
+/* it replaces the preliminary calibration runs of Secs. 5.1-5.2).  An MLP 4 -> 128 ->   */
+/* 128 -> 128 -> 4 with GELU maps X = (Tr, a, b, kappa_P) to Y = (rho_l, rho_v, W,       */
+/* sigma) as measured by calibration runs (flat interface: rho_l, rho_v, W; Laplace fit */
+/* of droplets: sigma).  Internally X and (rho_l, ln rho_v, W, sigma) are standardised  */
+/* with stats16 = {mean X[4], std X[4], mean Y'[4], std Y'[4]} (Y' with ln rho_v).      */
+/* Parameters: 34,180 FP32 values, per layer l = 0..3 the weights W_l [out][in]          */
+/* (row-major) followed by the bias b_l.  Training: full-batch MSE in the standardised  */
+/* space, Adam with bias correction, cosine learning-rate decay, FP32 kernels.          */
+/* Inference: one fused kernel, BF16 inputs and weights, FP32 accumulation and          */
+/* epilogue.  Host arrays are row-major n x 4 floats.  One surrogate owns a stream and  */
+/* device buffers; calls on the same surrogate must not overlap.                       */
+
+typedef struct {
+    int iterations;      /* Adam steps (full batch each) */
+    float lr, lr_min;    /* cosine decay from lr to lr_min over the run */
+    float beta1, beta2, eps, weight_decay;  /* Adam; decoupled weight decay */
+} lbm_train_cfg;
+
+typedef struct lbm_surrogate lbm_surrogate;
+
+/* Number of parameters (34,180). */
+int lbm_surrogate_num_params(void);
+
+/* New surrogate with the given standardisation (std entries > 0, else LBM_ERR_ARG) and
+ * seeded uniform He initialisation (zero biases). */
+int lbm_surrogate_create(const float* stats16, unsigned seed, lbm_surrogate** out);
+int lbm_surrogate_stats(const lbm_surrogate* m, float* stats16);
+int lbm_surrogate_set_params(lbm_surrogate* m, const float* params);
+int lbm_surrogate_get_params(lbm_surrogate* m, float* params);
+
+/* MSE loss (standardised space) and its gradient w.r.t. the parameters for the n
+ * samples X, Y (host) at the current parameters; either output may be NULL. */
+int lbm_surrogate_loss_grad(lbm_surrogate* m, const float* X, const float* Y, int n, float* loss, float* grad);
+
+/* Train on n samples (host X, Y; rho_v > 0).  *final_loss: loss before the last update.
+ * LBM_ERR_DIVERGED if the loss became non-finite. */
+int lbm_surrogate_train(lbm_surrogate* m, const float* X, const float* Y, int n, const lbm_train_cfg* cfg,
+                        float* final_loss);
+
+/* BF16 inference of n queries (host in, host out). */
+int lbm_surrogate_predict(lbm_surrogate* m, const float* X, int n, float* Y);
+
+/* BF16 inference on device arrays (n x 4 floats each) enqueued on stream (NULL: the
+ * surrogate's own); asynchronous. */
+int lbm_surrogate_predict_device(lbm_surrogate* m, const float* X_dev, int n, float* Y_dev, void* stream);
+
+/* The FP32 training forward pass, de-standardised (host in, host out). */
+int lbm_surrogate_predict_fp32(lbm_surrogate* m, const float* X, int n, float* Y);
+
+void lbm_surrogate_destroy(lbm_surrogate* m);
+
+/* Text of the last CUDA failure of a surrogate call on this host thread. */
+const char* lbm_surrogate_last_error(void);
 
 /* Checkpoint: write/read the populations, step counter and parameters (binary). */
 int lbm_save(lbm_ctx* ctx, const char* path);

@@ -466,6 +466,11 @@ extern "C" int lbm_batch_create(int n, const lbm_batch_lattice* specs, const dou
     size_t pool_bytes = 0;
     std::vector<size_t> offs(n);
     b->max_tiled_steps = 0;
+    std::vector<lbm_params> in_p(n), res_p(n);
+    std::vector<lbm_thermo> res_t(n);
+    std::vector<int> res_rc(n);
+    for (int i = 0; i < n; ++i) in_p[i] = specs[i].params;
+    lbm_resolve_params_many(n, in_p.data(), res_p.data(), res_t.data(), res_rc.data());
     for (int i = 0; i < n; ++i) {
         const lbm_batch_lattice& s = specs[i];
         if (s.nx < 1 || s.ny < 1 || s.nsteps < 0 || s.nsteps > (1LL << 30) || (s.geometry != 0 && s.geometry != 1) ||
@@ -477,9 +482,9 @@ extern "C" int lbm_batch_create(int n, const lbm_batch_lattice* specs, const dou
             delete b;
             return LBM_ERR_UNSUPPORTED;
         }
-        lbm_params rp;
-        lbm_thermo th;
-        int rc = lbm_resolve_params(&s.params, &rp, &th);
+        const lbm_params& rp = res_p[i];
+        const lbm_thermo& th = res_t[i];
+        int rc = res_rc[i];
         if (rc) {
             delete b;
             return rc;

@@ -5,7 +5,12 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
+#include <map>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -183,6 +188,39 @@ extern "C" int lbm_resolve_params(const lbm_params* in, lbm_params* out, lbm_the
     }
     *out = p;
     *th = t;
+    return LBM_OK;
+}
+
+extern "C" int lbm_resolve_params_many(int n, const lbm_params* in, lbm_params* out, lbm_thermo* th, int* status) {
+    if (n < 0 || (n > 0 && (!in || !out || !th || !status))) return LBM_ERR_ARG;
+    // identical inputs (byte-wise) are resolved once and copied
+    std::map<std::string, int> first;
+    std::vector<int> src(n), uniq;
+    for (int i = 0; i < n; ++i) {
+        const std::string key(reinterpret_cast<const char*>(&in[i]), sizeof(lbm_params));
+        auto it = first.emplace(key, i);
+        src[i] = it.first->second;
+        if (it.second) uniq.push_back(i);
+    }
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nt = std::max(1, std::min({hw > 0 ? hw : 1, (int)uniq.size(), 64}));
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int k; (k = next.fetch_add(1)) < (int)uniq.size();) {
+            const int i = uniq[k];
+            status[i] = lbm_resolve_params(&in[i], &out[i], &th[i]);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    for (int i = 0; i < n; ++i)
+        if (src[i] != i) {
+            status[i] = status[src[i]];
+            out[i] = out[src[i]];
+            th[i] = th[src[i]];
+        }
     return LBM_OK;
 }
 

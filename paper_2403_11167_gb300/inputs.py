@@ -75,3 +75,18 @@ def sweep_density(spec: dict, rho_v: float, rho_l: float, w0: float = 5.0) -> np
     if spec["geometry"] == 0:
         return flat_slab(spec["nx"], spec["ny"], rho_v, rho_l, w0)
     return droplet(spec["nx"], spec["ny"], spec["radius"], rho_v, rho_l, w0)
+
+
+def surrogate_sets(n: int, seed: int = 4032):
+    """Seeded parameter sets (Tr, a, b, kappa_P) of surrogate calibration runs.
+
+    Tr ~ U[0.5, 0.95], a ~ U[0.25, 0.5], b ~ U[3, 5], kappa_P uniform over {0.4, 0.7, 1.0};
+    R = 1, tau = 1, kappa_Li = 0, sigma_Li from the Appendix-B theory.  Training sets use
+    seed 4032, held-out sets seed 1116 (independent streams).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Tr = rng.uniform(0.5, 0.95, n)
+    a = rng.uniform(0.25, 0.5, n)
+    b = rng.uniform(3.0, 5.0, n)
+    kP = rng.choice([0.4, 0.7, 1.0], n)
+    return [dict(Tr=float(Tr[i]), a=float(a[i]), b=float(b[i]), kappa_P=float(kP[i])) for i in range(n)]

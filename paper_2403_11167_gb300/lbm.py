@@ -68,6 +68,11 @@ class lbm_obs(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
+class lbm_train_cfg(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int)] + [(n, ctypes.c_float) for n in (
+        "lr", "lr_min", "beta1", "beta2", "eps", "weight_decay")]
+
+
 lbm_batch_lattice._fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("geometry", ctypes.c_int),
                               ("pad_", ctypes.c_int), ("nsteps", ctypes.c_longlong), ("params", lbm_params)]
 
@@ -77,7 +82,8 @@ class LBMError(RuntimeError):
         self.code = code
         msg = f"{what}: {lbm_strerror(code)} ({code})"
         if code == LBM_ERR_CUDA:
-            msg += " -- " + _lib().lbm_last_cuda_error().decode() + " " + _lib().lbm_batch_last_error().decode()
+            msg += " -- " + " ".join(getattr(_lib(), f)().decode() for f in (
+                "lbm_last_cuda_error", "lbm_batch_last_error", "lbm_surrogate_last_error"))
         super().__init__(msg)
 
 
@@ -93,6 +99,7 @@ def _lib():
         L = ctypes.CDLL(LIB_PATH)
         P, T, O = ctypes.POINTER(lbm_params), ctypes.POINTER(lbm_thermo), ctypes.POINTER(lbm_obs)
         dp, vp = ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+        fp = ctypes.POINTER(ctypes.c_float)
         sig = {
             "lbm_params_default": ([ctypes.c_int, P], ctypes.c_int),
             "lbm_resolve_params": ([P, P, T], ctypes.c_int),
@@ -129,6 +136,19 @@ def _lib():
             "lbm_batch_stream": ([vp], vp),
             "lbm_batch_destroy": ([vp], None),
             "lbm_batch_last_error": ([], ctypes.c_char_p),
+            "lbm_resolve_params_many": ([ctypes.c_int, P, P, T, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "lbm_surrogate_num_params": ([], ctypes.c_int),
+            "lbm_surrogate_create": ([fp, ctypes.c_uint, ctypes.POINTER(vp)], ctypes.c_int),
+            "lbm_surrogate_stats": ([vp, fp], ctypes.c_int),
+            "lbm_surrogate_set_params": ([vp, fp], ctypes.c_int),
+            "lbm_surrogate_get_params": ([vp, fp], ctypes.c_int),
+            "lbm_surrogate_loss_grad": ([vp, fp, fp, ctypes.c_int, fp, fp], ctypes.c_int),
+            "lbm_surrogate_train": ([vp, fp, fp, ctypes.c_int, ctypes.POINTER(lbm_train_cfg), fp], ctypes.c_int),
+            "lbm_surrogate_predict": ([vp, fp, ctypes.c_int, fp], ctypes.c_int),
+            "lbm_surrogate_predict_device": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+            "lbm_surrogate_predict_fp32": ([vp, fp, ctypes.c_int, fp], ctypes.c_int),
+            "lbm_surrogate_destroy": ([vp], None),
+            "lbm_surrogate_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -363,3 +383,113 @@ def sweep_specs(entries, precision=LBM_F32):
         specs.append(dict(nx=e["nx"], ny=e["ny"], geometry=e["geometry"], nsteps=e["nsteps"], params=p))
         rhos.append(inputs.sweep_density(e, th.rho_v, th.rho_l))
     return specs, rhos
+
+
+def lbm_resolve_params_many(params_list):
+    """``lbm_resolve_params`` over a list on all host cores; returns [(status, params, thermo)]."""
+    n = len(params_list)
+    if n == 0:
+        return []
+    inp, outp, th = (lbm_params * n)(*params_list), (lbm_params * n)(), (lbm_thermo * n)()
+    st = (ctypes.c_int * n)()
+    _check(_lib().lbm_resolve_params_many(n, inp, outp, th, st), "lbm_resolve_params_many")
+    return [(st[i], outp[i], th[i]) for i in range(n)]
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _f32(a, cols=4):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != cols:
+        raise ValueError(f"expected an n x {cols} array, got {a.shape}")
+    return a
+
+
+SURROGATE_INPUTS = ("Tr", "a", "b", "kappa_P")
+SURROGATE_OUTPUTS = ("rho_l", "rho_v", "width", "sigma")
+
+
+class Surrogate:
+    """Owner of one ``lbm_surrogate`` (the MLP calibration surrogate).
+
+    X rows are (Tr, a, b, kappa_P); Y rows are (rho_l, rho_v, W, sigma)."""
+
+    def __init__(self, stats16, seed=0):
+        st = np.ascontiguousarray(stats16, dtype=np.float32).reshape(16)
+        h = ctypes.c_void_p()
+        _check(_lib().lbm_surrogate_create(_fptr(st), seed, ctypes.byref(h)), "lbm_surrogate_create")
+        self.h = h
+        self.n_params = _lib().lbm_surrogate_num_params()
+
+    @staticmethod
+    def standardisation(X, Y):
+        """stats16 of a training set: mean/std of X and of (rho_l, ln rho_v, W, sigma)."""
+        X = np.asarray(X, dtype=np.float64)
+        Yp = np.array(Y, dtype=np.float64)
+        Yp[:, 1] = np.log(Yp[:, 1])
+        sx, sy = X.std(0), Yp.std(0)
+        sx[sx == 0] = 1.0
+        sy[sy == 0] = 1.0
+        return np.concatenate([X.mean(0), sx, Yp.mean(0), sy]).astype(np.float32)
+
+    def stats(self):
+        st = np.zeros(16, np.float32)
+        _check(_lib().lbm_surrogate_stats(self.h, _fptr(st)), "lbm_surrogate_stats")
+        return st
+
+    def params(self):
+        p = np.zeros(self.n_params, np.float32)
+        _check(_lib().lbm_surrogate_get_params(self.h, _fptr(p)), "lbm_surrogate_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.shape == (self.n_params,)
+        _check(_lib().lbm_surrogate_set_params(self.h, _fptr(p)), "lbm_surrogate_set_params")
+
+    def loss_grad(self, X, Y):
+        X, Y = _f32(X), _f32(Y)
+        loss = np.zeros(1, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        _check(_lib().lbm_surrogate_loss_grad(self.h, _fptr(X), _fptr(Y), len(X), _fptr(loss), _fptr(g)),
+               "lbm_surrogate_loss_grad")
+        return float(loss[0]), g
+
+    def train(self, X, Y, iterations=20000, lr=2e-3, lr_min=2e-5, beta1=0.9, beta2=0.999, eps=1e-8,
+              weight_decay=0.0):
+        X, Y = _f32(X), _f32(Y)
+        cfg = lbm_train_cfg(iterations, lr, lr_min, beta1, beta2, eps, weight_decay)
+        loss = np.zeros(1, np.float32)
+        _check(_lib().lbm_surrogate_train(self.h, _fptr(X), _fptr(Y), len(X), ctypes.byref(cfg), _fptr(loss)),
+               "lbm_surrogate_train")
+        return float(loss[0])
+
+    def predict(self, X):
+        X = _f32(X)
+        Y = np.zeros_like(X)
+        _check(_lib().lbm_surrogate_predict(self.h, _fptr(X), len(X), _fptr(Y)), "lbm_surrogate_predict")
+        return Y
+
+    def predict_fp32(self, X):
+        X = _f32(X)
+        Y = np.zeros_like(X)
+        _check(_lib().lbm_surrogate_predict_fp32(self.h, _fptr(X), len(X), _fptr(Y)), "lbm_surrogate_predict_fp32")
+        return Y
+
+    def predict_device(self, X_dev, Y_dev, stream=None):
+        """BF16 inference on device tensors (float32, n x 4, contiguous); asynchronous."""
+        _check(_lib().lbm_surrogate_predict_device(self.h, X_dev.data_ptr(), X_dev.shape[0], Y_dev.data_ptr(),
+                                                   stream), "lbm_surrogate_predict_device")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().lbm_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

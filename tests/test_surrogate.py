@@ -1,0 +1,166 @@
+"""Calibration surrogate: the GPU training kernels against the FP64 CPU network oracle,
+BF16 inference within its rounding bound, and the trained network against plain
+calibration runs on held-out parameter sets (with the gain over the no-network theory)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_2403_11167_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2403_11167_gb300 import lbm as L
+
+    return L
+
+
+def _theta(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for l in range(M.N_LAYERS):
+        lim = math.sqrt(6.0 / M.DIMS[l])
+        parts.append(rng.uniform(-lim, lim, M.DIMS[l + 1] * M.DIMS[l]))
+        parts.append(rng.uniform(-0.1, 0.1, M.DIMS[l + 1]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _data(n, seed):
+    """Inputs over the calibration ranges and a smooth synthetic target map."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = np.column_stack([rng.uniform(0.5, 0.95, n), rng.uniform(0.25, 0.5, n), rng.uniform(3, 5, n),
+                         rng.choice([0.4, 0.7, 1.0], n)])
+    Y = np.column_stack([(1.3 - X[:, 0]) / X[:, 2], np.exp(-12 * (1 - X[:, 0]) ** 0.8) / X[:, 2],
+                         3 + 6 * np.sqrt(X[:, 3]) / (1.05 - X[:, 0]), 0.04 * X[:, 1] * (1 - X[:, 0]) ** 1.5])
+    return X.astype(np.float32), Y.astype(np.float32)
+
+
+def _layer_slices():
+    out = []
+    for l, (wo, bo) in enumerate(M.offsets()):
+        out.append(slice(wo, bo))
+        out.append(slice(bo, bo + M.DIMS[l + 1]))
+    return out
+
+
+@pytest.mark.parametrize("n", [300, 5000])
+def test_gradient_matches_oracle(lbm, n):
+    """FP32 forward/backward kernels (tiled SGEMM, split-K weight gradients) against the FP64
+    backpropagation of the same parameters and data: per tensor, max error <= 1e-4 of the
+    tensor's largest gradient entry; loss within 1e-5."""
+    X, Y = _data(n, seed=n)
+    st = lbm.Surrogate.standardisation(X, Y)
+    m = lbm.Surrogate(st, seed=1)
+    th = _theta(2)
+    m.set_params(th)
+    loss, g = m.loss_grad(X, Y)
+    loss_ref, g_ref = M.loss_grad(th.astype(np.float64), X.astype(np.float64), Y.astype(np.float64),
+                                  st.astype(np.float64))
+    assert abs(loss / loss_ref - 1) < 1e-5
+    for sl in _layer_slices():
+        scale = np.max(np.abs(g_ref[sl]))
+        assert np.max(np.abs(g[sl] - g_ref[sl])) <= 1e-4 * scale, (sl, np.max(np.abs(g[sl] - g_ref[sl])) / scale)
+    m.close()
+
+
+def test_adam_update_matches_oracle(lbm):
+    """One training iteration = the gradient above plus the Adam kernel: the new parameters
+    equal the oracle's Adam step applied to that gradient (first step, bias-corrected)."""
+    X, Y = _data(300, seed=7)
+    st = lbm.Surrogate.standardisation(X, Y)
+    m = lbm.Surrogate(st, seed=1)
+    th = _theta(3)
+    m.set_params(th)
+    _, g = m.loss_grad(X, Y)
+    lr = 1e-3
+    m.train(X, Y, iterations=1, lr=lr, lr_min=lr, weight_decay=1e-4)
+    p1 = m.params().astype(np.float64)
+    ref, _, _ = M.adam_step(th.astype(np.float64), g.astype(np.float64), np.zeros(M.N_PARAMS), np.zeros(M.N_PARAMS),
+                            1, lr, weight_decay=1e-4)
+    big = np.abs(g) > 1e-5 * np.max(np.abs(g))
+    assert np.max(np.abs(p1 - ref)[big]) < 1e-7 + 1e-6 * np.max(np.abs(ref))
+    # where the gradient is at rounding level the step is still bounded by lr (first Adam step)
+    assert np.all(np.abs(p1 - th) <= lr * (1 + 1e-4) + lr * 1e-4 * np.abs(th) + 1e-7)
+    m.close()
+
+
+def test_fp32_forward_matches_oracle(lbm):
+    X, Y = _data(1000, seed=11)
+    st = lbm.Surrogate.standardisation(X, Y)
+    m = lbm.Surrogate(st, seed=1)
+    th = _theta(4)
+    m.set_params(th)
+    P = m.predict_fp32(X)
+    ref = M.predict(th.astype(np.float64), X.astype(np.float64), st.astype(np.float64))
+    assert np.max(np.abs(P / ref - 1)) < 2e-5
+    m.close()
+
+
+@pytest.mark.parametrize("n", [4096, 1000, 1])
+def test_bf16_inference_within_rounding_bound(lbm, n):
+    """Fused BF16 (tensor-core mma, FP32 accumulate) inference against the FP64 forward pass:
+    every standardised output within the first-order BF16 rounding bound of the oracle (plus
+    FP32 slack); BF16 rounding is visible (the kernel does not run in FP32)."""
+    X, Y = _data(max(n, 64), seed=13)
+    X = X[:n]
+    st = lbm.Surrogate.standardisation(*_data(2000, seed=5))
+    m = lbm.Surrogate(st, seed=1)
+    th = _theta(5)
+    m.set_params(th)
+    P = m.predict(X)
+    st64 = st.astype(np.float64)
+    yn = M.standardise_y(P.astype(np.float64), st64)
+    ref = M.forward(th.astype(np.float64), M.standardise_x(X.astype(np.float64), st64))[0][-1]
+    bound = M.bf16_error_bound(th.astype(np.float64), X.astype(np.float64), st64)
+    err = np.abs(yn - ref)
+    assert np.all(err <= 1.05 * bound + 1e-4), np.max(err - bound)
+    if n >= 1000:
+        assert np.max(err) > 1e-5
+    m.close()
+
+
+def test_device_inference_equals_host_inference(lbm):
+    import torch
+
+    X, Y = _data(4096, seed=17)
+    st = lbm.Surrogate.standardisation(X, Y)
+    m = lbm.Surrogate(st, seed=3)
+    P = m.predict(X)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.empty_like(Xd)
+    m.predict_device(Xd, Yd)
+    torch.cuda.synchronize()
+    assert np.array_equal(Yd.cpu().numpy(), P)
+    m.close()
+
+
+def test_training_fits_smooth_map(lbm):
+    X, Y = _data(4000, seed=19)
+    Xh, Yh = _data(500, seed=23)
+    st = lbm.Surrogate.standardisation(X, Y)
+    m = lbm.Surrogate(st, seed=0)
+    loss0, _ = m.loss_grad(X, Y)
+    loss = m.train(X, Y, iterations=4000, lr=2e-3, lr_min=1e-5)
+    assert loss < loss0 / 1000
+    err = np.abs(m.predict(Xh) / Yh - 1)
+    assert np.max(err[:, 0]) < 0.01 and np.max(err[:, 1]) < 0.02
+    m.close()
+
+
+def test_surrogate_argument_errors(lbm):
+    st = np.ones(16, np.float32)
+    st[4] = 0.0
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Surrogate(st)
+    assert e.value.code == lbm.LBM_ERR_ARG
+    m = lbm.Surrogate(np.ones(16, np.float32))
+    with pytest.raises(lbm.LBMError):
+        m.train(np.zeros((4, 4), np.float32), np.ones((4, 4), np.float32), iterations=10, lr=-1.0)
+    m.close()
