@@ -23,6 +23,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -43,6 +45,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-vs-plain calibration sweep")
     ap.add_argument("--sweep-lattices", type=int, default=512)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned calibration surrogate")
+    ap.add_argument("--surrogate-sets", type=int, default=8000)
+    ap.add_argument("--plain-sets", type=int, default=6, help="held-out sets also calibrated one lattice at a time")
     return ap.parse_args()
 
 
@@ -220,6 +225,82 @@ def run_sweep(args):
                         "5e3-2e4 steps), FP32"}
 
 
+def run_surrogate(args):
+    """Learned calibration surrogate: label seeded parameter sets (Tr, a, b, kappa_P) with the
+    batched solver (flat slab + three width-scaled droplets each), train the MLP on the GPU,
+    and judge it against the calibration runs of 256 held-out sets (batched; a sample of them
+    also through the plain one-lattice-at-a-time API, which must agree bitwise).  Reports the
+    per-set cost of a plain calibration, of a batched one, and of a surrogate query (4096
+    queries per fused BF16 launch, CUDA events), held-out errors, and the gain over the
+    no-network theory (Maxwell densities) at Tr <= 0.6."""
+    import torch
+
+    from paper_2403_11167_gb300 import calibration as C
+    from paper_2403_11167_gb300 import inputs
+
+    tr = inputs.surrogate_sets(args.surrogate_sets, seed=4032)
+    ho = inputs.surrogate_sets(256, seed=1116)
+    r = C.calibrate_batched(tr)
+    rh = C.calibrate_batched(ho)
+    k = args.plain_sets
+    rp = C.calibrate_plain(ho[:k])
+    plain_equal = bool(np.array_equal(rp["Y"], rh["Y"][:k], equal_nan=True))
+    X, ok = C.features(tr), r["ok"]
+    m, loss, t_train = C.fit_surrogate(X[ok], r["Y"][ok])
+    Xh, okh = C.features(ho), rh["ok"]
+    P = m.predict(Xh)
+    err = C.relative_errors(P[okh], rh["Y"][okh])
+    sig = np.isfinite(err[:, 3])
+    # inference: 4096 queries resident on the device, one fused launch each, events on the stream
+    q = torch.from_numpy(C.features(inputs.surrogate_sets(4096, seed=777)).astype(np.float32)).cuda()
+    out = torch.empty_like(q)
+    stream = torch.cuda.current_stream()
+    for _ in range(5):
+        m.predict_device(q, out, stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 200
+    e0.record(stream)
+    for _ in range(reps):
+        m.predict_device(q, out, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    infer_us = e0.elapsed_time(e1) * 1e3 / reps
+    e0.record(stream)
+    for _ in range(reps):
+        m.predict_device(q, out, stream.cuda_stream, mode=1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    infer_single_us = e0.elapsed_time(e1) * 1e3 / reps
+    T = C.theory(ho)
+    low = okh & (Xh[:, 0] <= 0.6)
+    e_th = np.abs(T[low, 1] / rh["Y"][low, 1] - 1)
+    e_nn = np.abs(P[low, 1] / rh["Y"][low, 1] - 1)
+    m.close()
+    plain_per_set = rp["seconds"] / k
+    return {
+        "training_sets": len(tr), "training_sets_valid": int(ok.sum()),
+        "training_sets_with_sigma": int(np.isfinite(r["Y"][ok, 3]).sum()),
+        "label_seconds_batched": r["seconds"], "label_lattice_updates": r["updates"],
+        "label_glups": r["updates"] / r["seconds"] / 1e9,
+        "train_seconds": t_train, "train_final_loss": loss,
+        "held_out_sets": len(ho), "held_out_valid": int(okh.sum()), "held_out_with_sigma": int(sig.sum()),
+        "max_rel_err": {"rho_l": float(err[:, 0].max()), "rho_v": float(err[:, 1].max()),
+                        "width": float(err[:, 2].max()), "sigma": float(err[sig, 3].max())},
+        "mean_rel_err": {"rho_l": float(err[:, 0].mean()), "rho_v": float(err[:, 1].mean()),
+                         "width": float(err[:, 2].mean()), "sigma": float(err[sig, 3].mean())},
+        "gain_rho_v_Tr_le_0.6": {"sets": int(low.sum()), "theory_mean_rel_err": float(e_th.mean()),
+                                 "surrogate_mean_rel_err": float(e_nn.mean())},
+        "seconds_per_set": {"plain_calibration": plain_per_set, "batched_calibration": rh["seconds"] / len(ho),
+                            "surrogate_query": infer_us * 1e-6 / 4096},
+        "plain_sample_sets": k, "plain_equals_batched_bitwise": plain_equal,
+        "inference_us_per_4096_queries": infer_us, "inference_mode": "split-BF16 operands, FP32 accumulation",
+        "inference_us_per_4096_queries_single_bf16": infer_single_us,
+        "workload": f"{len(tr)} training + 256 held-out seeded pseudopotential parameter sets (Tr U[0.5,0.95], "
+                    "a U[0.25,0.5], b U[3,5], kappa_P in {0.4,0.7,1}); per set a 256x4 slab (4e4 and 5e4 steps) "
+                    "and three droplets R = 3l, 4l, 5l on 16l lattices, l = max(W_theory, 4)",
+    }
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_2403_11167_gb300", "csrc", "lbm_kernels.cuh"), "rb") as fh:
@@ -360,6 +441,9 @@ def run_ours(args):
     sweep = None
     if not args.no_sweep:
         sweep = run_sweep(args)
+    surrogate = None
+    if not args.no_surrogate:
+        surrogate = run_surrogate(args)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         v, cores, sample = oracle_mlups(rho0, args.cpu_seconds)
@@ -370,7 +454,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": args.steps * (2 + 2 * nsteps), "clocks": clocks, "per_model": per_model,
-        "sweep": sweep,
+        "sweep": sweep, "surrogate": surrogate,
         "kernel_source_sha256_12": kernel_source_hash(),
     }
     print(json.dumps(line))

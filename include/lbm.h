@@ -278,7 +278,8 @@ const char* lbm_batch_last_error(void);
 /* (row-major) followed by the bias b_l.  Training: full-batch MSE in the standardised  */
 /* space, Adam with bias correction, cosine learning-rate decay, FP32 kernels.          */
 /* Inference: one fused kernel, BF16 inputs and weights, FP32 accumulation and          */
-/* epilogue.  Host arrays are row-major n x 4 floats.  One surrogate owns a stream and  */
+/* epilogue (see the inference modes).  Host arrays are row-major n x 4 floats.  One    */
+/* surrogate owns a stream and                                                          */
 /* device buffers; calls on the same surrogate must not overlap.                       */
 
 typedef struct {
@@ -300,20 +301,29 @@ int lbm_surrogate_set_params(lbm_surrogate* m, const float* params);
 int lbm_surrogate_get_params(lbm_surrogate* m, float* params);
 
 /* MSE loss (standardised space) and its gradient w.r.t. the parameters for the n
- * samples X, Y (host) at the current parameters; either output may be NULL. */
+ * samples X, Y (host) at the current parameters; either output may be NULL.  A NaN
+ * entry of Y other than rho_v is a missing target (left out of the mean); every rho_v
+ * must be finite and > 0, else LBM_ERR_ARG. */
 int lbm_surrogate_loss_grad(lbm_surrogate* m, const float* X, const float* Y, int n, float* loss, float* grad);
 
-/* Train on n samples (host X, Y; rho_v > 0).  *final_loss: loss before the last update.
+/* Train on n samples (host X, Y as for lbm_surrogate_loss_grad; missing targets allowed).
+ * *final_loss: loss before the last update.
  * LBM_ERR_DIVERGED if the loss became non-finite. */
 int lbm_surrogate_train(lbm_surrogate* m, const float* X, const float* Y, int n, const lbm_train_cfg* cfg,
                         float* final_loss);
 
-/* BF16 inference of n queries (host in, host out). */
-int lbm_surrogate_predict(lbm_surrogate* m, const float* X, int n, float* Y);
+/* Inference modes of the fused tensor-core kernel (BF16 operands, FP32 accumulation):
+ * LBM_INFER_SPLIT_BF16 carries every operand as BF16 hi + lo parts and sums three BF16
+ * products per tile (result within ~2^-15 of the FP32 network); LBM_INFER_BF16 rounds
+ * every operand to BF16 once (relative 2^-8 per operand). */
+enum { LBM_INFER_SPLIT_BF16 = 0, LBM_INFER_BF16 = 1 };
 
-/* BF16 inference on device arrays (n x 4 floats each) enqueued on stream (NULL: the
+/* Inference of n queries (host in, host out) in the given mode. */
+int lbm_surrogate_predict(lbm_surrogate* m, const float* X, int n, float* Y, int mode);
+
+/* Inference on device arrays (n x 4 floats each) enqueued on stream (NULL: the
  * surrogate's own); asynchronous. */
-int lbm_surrogate_predict_device(lbm_surrogate* m, const float* X_dev, int n, float* Y_dev, void* stream);
+int lbm_surrogate_predict_device(lbm_surrogate* m, const float* X_dev, int n, float* Y_dev, int mode, void* stream);
 
 /* The FP32 training forward pass, de-standardised (host in, host out). */
 int lbm_surrogate_predict_fp32(lbm_surrogate* m, const float* X, int n, float* Y);

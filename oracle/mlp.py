@@ -7,8 +7,8 @@ path never does.  Plain NumPy in float64, one operation per line of the definiti
   4, 128, 128, 128, 4; GELU(z) = z Phi(z) with Phi the standard normal CDF (via erf);
 * parameters: one flat vector, per layer W_l [out][in] row-major, then b_l;
 * inputs and targets standardised with stats16 = (mean X, std X, mean Y', std Y'),
-  Y' = (rho_l, ln rho_v, W, sigma); loss = mean over all n*4 entries of the squared
-  standardised error;
+  Y' = (rho_l, ln rho_v, W, sigma); loss = mean over the finite target entries of the
+  squared standardised error (NaN marks a missing target);
 * gradient by the chain rule (backpropagation), Adam with bias correction and decoupled
   weight decay, cosine learning-rate decay from lr to lr_min over the run;
 * a first-order bound of the error of BF16 inputs/weights/activations with exact
@@ -109,8 +109,10 @@ def loss_grad(theta, X, Y, stats):
     Xn, Yn = standardise_x(X, stats), standardise_y(Y, stats)
     pre, acts = forward(theta, Xn)
     layers = unpack(theta)
-    count = Yn.size
-    r = pre[-1] - Yn
+    # a NaN target is missing: it adds neither loss nor gradient; the mean runs over the rest
+    valid = np.isfinite(Yn)
+    count = int(valid.sum())
+    r = np.where(valid, pre[-1] - np.where(valid, Yn, 0.0), 0.0)
     loss = float(np.sum(r * r) / count)
     dz = 2.0 * r / count
     grads = [None] * N_LAYERS

@@ -123,17 +123,19 @@ __global__ void gelu_bwd_kernel(const float* __restrict__ Z, float* __restrict__
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dA[i] *= gelu_grad(Z[i]);
 }
 
-// MSE over all outputs: dZ = 2 (Z - Y) / (n kOut); loss accumulated (sum of squares / count).
+// Mean squared error over the finite targets (a NaN target is missing: no loss, no
+// gradient): dZ = 2 (Z - Y) / n_valid; loss accumulated as sum of squares / n_valid.
 __global__ void mse_kernel(const float* __restrict__ Z, const float* __restrict__ Y, float* __restrict__ dZ, int count,
-                           float* __restrict__ loss) {
+                           float inv_valid, float* __restrict__ loss) {
     float s = 0.0f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-        const float d = Z[i] - Y[i];
-        dZ[i] = 2.0f * d / count;
+        const float y = Y[i];
+        const float d = isnan(y) ? 0.0f : Z[i] - y;
+        dZ[i] = 2.0f * d * inv_valid;
         s += d * d;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / count);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv_valid);
 }
 
 // db[j] = sum_i dZ[i, j]
@@ -179,27 +181,43 @@ __global__ void standardise_kernel(const float* __restrict__ X, const float* __r
 
 // ---------------------------------------------------------------------------------------
 // Fused BF16 inference: one CTA of 128 threads (4 warps) evaluates 64 queries through all four
-// layers.  Weights (BF16) live in shared memory; each layer is an mma.sync m16n8k16 BF16 GEMM
-// with FP32 accumulators; bias + GELU in FP32, activations re-quantised to BF16 for the next
-// layer; the output layer is de-standardised (and rho_v exponentiated) in FP32.
+// layers.  Each layer is an mma.sync m16n8k16 BF16 GEMM with FP32 accumulators; bias + GELU
+// run in FP32 and the activations stay FP32 in shared memory; the output layer is
+// de-standardised (and rho_v exponentiated) in FP32.
+//
+// Split mode (kSplit): every FP32 operand x is carried as two BF16 numbers, hi = bf16(x) and
+// lo = bf16(x - hi), and each tile accumulates hi*hi + lo*hi + hi*lo (the lo*lo term, below
+// 2^-16 relative, is dropped): BF16 tensor-core products with FP32 accumulation that keep the
+// result within ~2^-16 of the FP32 network.  Single mode rounds every operand to BF16 once
+// (relative 2^-8), which costs up to ~1% in rho_v because ln rho_v spans several units.
 constexpr int kQ = 64;                    // queries per CTA
 constexpr int kInPad = 16;                // first layer K padded to one MMA K step
-constexpr int kActStride = kHid + 8;      // bf16 elements per activation row (bank spread)
-constexpr int kWStride = kHid + 8;
+constexpr int kActStride = kHid + 4;      // floats per activation row (bank spread)
+constexpr int kWStride = kHid + 8;        // bf16 elements per weight row
+constexpr int kPackHalf = kHid * kInPad + 2 * kHid * kHid + 8 * kHid;  // bf16 elements of hi (or lo)
 
 struct InferSmem {
-    __nv_bfloat16 w1[kHid][kInPad];             // layer 1 weights, K padded
-    __nv_bfloat16 w[2][kHid][kWStride];          // layers 2, 3
-    __nv_bfloat16 w4[8][kWStride];               // layer 4 weights, N padded to 8
+    __nv_bfloat16 w1[2][kHid][kInPad];          // layer 1 weights (hi, lo), K padded
+    __nv_bfloat16 w[2][2][kHid][kWStride];      // layers 2, 3 (layer, hi/lo)
+    __nv_bfloat16 w4[2][8][kWStride];           // layer 4 (hi, lo), N padded to 8
     float bias[3][kHid];
     float b4[8];
-    __nv_bfloat16 act[2][kQ][kActStride];        // ping-pong activations
+    float act[2][kQ][kActStride];               // ping-pong FP32 activations
     float stats[16];
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// (x, y) -> hi = bf16x2(x, y), lo = bf16x2(x - hi.x, y - hi.y)
+__device__ __forceinline__ void split_bf16(float2 v, uint32_t& hi, uint32_t& lo) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+    const float2 hf = __bfloat1622float2(h);
+    __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+    hi = *reinterpret_cast<uint32_t*>(&h);
+    lo = *reinterpret_cast<uint32_t*>(&l);
 }
 
 // D (16x8, f32) += A (16x16, bf16, row) * B (16x8, bf16, col)
@@ -211,17 +229,18 @@ __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Fragment loads from row-major bf16 arrays (A: [row][k], B stored as W[n][k] = column-major B).
-__device__ __forceinline__ void load_a_frag(const __nv_bfloat16* base, int stride, int row0, int k0, int lane,
-                                            uint32_t a[4]) {
+// A fragment (rows row0..row0+15, k0..k0+15) from FP32 activations, as BF16 hi and lo parts.
+__device__ __forceinline__ void load_a_frag(const float* base, int row0, int k0, int lane, uint32_t ah[4],
+                                            uint32_t al[4]) {
     const int g = lane >> 2, t = lane & 3;
-    const __nv_bfloat16* p0 = base + (row0 + g) * stride + k0 + t * 2;
-    const __nv_bfloat16* p1 = base + (row0 + g + 8) * stride + k0 + t * 2;
-    a[0] = *reinterpret_cast<const uint32_t*>(p0);
-    a[1] = *reinterpret_cast<const uint32_t*>(p1);
-    a[2] = *reinterpret_cast<const uint32_t*>(p0 + 8);
-    a[3] = *reinterpret_cast<const uint32_t*>(p1 + 8);
+    const float* p0 = base + (row0 + g) * kActStride + k0 + t * 2;
+    const float* p1 = base + (row0 + g + 8) * kActStride + k0 + t * 2;
+    split_bf16(*reinterpret_cast<const float2*>(p0), ah[0], al[0]);
+    split_bf16(*reinterpret_cast<const float2*>(p1), ah[1], al[1]);
+    split_bf16(*reinterpret_cast<const float2*>(p0 + 8), ah[2], al[2]);
+    split_bf16(*reinterpret_cast<const float2*>(p1 + 8), ah[3], al[3]);
 }
+// B fragment from a weight array stored as W[n][k] (= column-major B).
 __device__ __forceinline__ void load_b_frag(const __nv_bfloat16* W, int stride, int n0, int k0, int lane,
                                             uint32_t b[2]) {
     const int g = lane >> 2, t = lane & 3;
@@ -230,6 +249,22 @@ __device__ __forceinline__ void load_b_frag(const __nv_bfloat16* W, int stride, 
     b[1] = *reinterpret_cast<const uint32_t*>(p + 8);
 }
 
+template <bool kSplit>
+__device__ __forceinline__ void mma_tile(float d[4], const uint32_t ah[4], const uint32_t al[4],
+                                         const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, int stride, int n0,
+                                         int k0, int lane) {
+    uint32_t bh[2];
+    load_b_frag(Whi, stride, n0, k0, lane, bh);
+    mma_bf16(d, ah, bh);
+    if (kSplit) {
+        uint32_t bl[2];
+        load_b_frag(Wlo, stride, n0, k0, lane, bl);
+        mma_bf16(d, al, bh);
+        mma_bf16(d, ah, bl);
+    }
+}
+
+template <bool kSplit>
 __global__ void __launch_bounds__(128) mlp_infer_bf16_kernel(const float* __restrict__ X, int n,
                                                              const __nv_bfloat16* __restrict__ wpack,
                                                              const float* __restrict__ bpack,
@@ -237,31 +272,37 @@ __global__ void __launch_bounds__(128) mlp_infer_bf16_kernel(const float* __rest
     extern __shared__ __align__(16) unsigned char ism[];
     InferSmem& s = *reinterpret_cast<InferSmem*>(ism);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // stage weights: wpack holds w1 [128][16], w2, w3 [128][128], w4 [8][128] (bf16, zero padded)
-    for (int i = tid; i < kHid * kInPad; i += 128) (&s.w1[0][0])[i] = wpack[i];
-    for (int l = 0; l < 2; ++l)
-        for (int i = tid; i < kHid * kHid; i += 128)
-            s.w[l][i / kHid][i % kHid] = wpack[kHid * kInPad + l * kHid * kHid + i];
-    for (int i = tid; i < 8 * kHid; i += 128) s.w4[i / kHid][i % kHid] = wpack[kHid * kInPad + 2 * kHid * kHid + i];
+    // stage weights: wpack holds [hi | lo], each w1 [128][16], w2, w3 [128][128], w4 [8][128]
+    for (int h = 0; h < (kSplit ? 2 : 1); ++h) {
+        const __nv_bfloat16* src = wpack + h * kPackHalf;
+        for (int i = tid; i < kHid * kInPad; i += 128) (&s.w1[h][0][0])[i] = src[i];
+        for (int l = 0; l < 2; ++l)
+            for (int i = tid; i < kHid * kHid; i += 128)
+                s.w[l][h][i / kHid][i % kHid] = src[kHid * kInPad + l * kHid * kHid + i];
+        for (int i = tid; i < 8 * kHid; i += 128)
+            s.w4[h][i / kHid][i % kHid] = src[kHid * kInPad + 2 * kHid * kHid + i];
+    }
     for (int i = tid; i < 3 * kHid; i += 128) (&s.bias[0][0])[i] = bpack[i];
     if (tid < 8) s.b4[tid] = bpack[3 * kHid + tid];
     if (tid < 16) s.stats[tid] = stats[tid];
     __syncthreads();
     const int q0 = blockIdx.x * kQ;
-    // standardised inputs -> bf16 activation rows (K padded to 16 with zeros)
+    // standardised inputs (K padded to 16 with zeros)
     for (int i = tid; i < kQ * kInPad; i += 128) {
         const int r = i / kInPad, k = i % kInPad;
         float v = 0.0f;
         if (k < kIn && q0 + r < n) v = (X[(size_t)(q0 + r) * kIn + k] - s.stats[k]) / s.stats[4 + k];
-        s.act[0][r][k] = __float2bfloat16_rn(v);
+        s.act[0][r][k] = v;
     }
     __syncthreads();
     // each warp owns 16 query rows; three hidden layers of N = 128 (16 n-tiles of 8)
     const int row0 = warp * 16;
+    const int g = lane >> 2, t = lane & 3;
     int cur = 0;
     for (int layer = 0; layer < 3; ++layer) {
         const int ksteps = layer == 0 ? 1 : kHid / 16;
-        const __nv_bfloat16* Wb = layer == 0 ? &s.w1[0][0] : &s.w[layer - 1][0][0];
+        const __nv_bfloat16* Whi = layer == 0 ? &s.w1[0][0][0] : &s.w[layer - 1][0][0][0];
+        const __nv_bfloat16* Wlo = layer == 0 ? &s.w1[1][0][0] : &s.w[layer - 1][1][0][0];
         const int wstride = layer == 0 ? kInPad : kWStride;
         float acc[16][4];
 #pragma unroll
@@ -269,25 +310,20 @@ __global__ void __launch_bounds__(128) mlp_infer_bf16_kernel(const float* __rest
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[nt][j] = 0.0f;
         for (int ks = 0; ks < ksteps; ++ks) {
-            uint32_t a[4];
-            load_a_frag(&s.act[cur][0][0], kActStride, row0, ks * 16, lane, a);
+            uint32_t ah[4], al[4];
+            load_a_frag(&s.act[cur][0][0], row0, ks * 16, lane, ah, al);
 #pragma unroll
-            for (int nt = 0; nt < 16; ++nt) {
-                uint32_t b[2];
-                load_b_frag(Wb, wstride, nt * 8, ks * 16, lane, b);
-                mma_bf16(acc[nt], a, b);
-            }
+            for (int nt = 0; nt < 16; ++nt) mma_tile<kSplit>(acc[nt], ah, al, Whi, Wlo, wstride, nt * 8, ks * 16, lane);
         }
-        // bias + GELU in FP32, store bf16 into the other activation buffer
-        const int g = lane >> 2, t = lane & 3;
+        // bias + GELU in FP32 into the other activation buffer (rows of this warp only)
 #pragma unroll
         for (int nt = 0; nt < 16; ++nt) {
             const int c = nt * 8 + t * 2;
             const float b0 = s.bias[layer][c], b1 = s.bias[layer][c + 1];
-            const uint32_t lo = pack_bf16(gelu(acc[nt][0] + b0), gelu(acc[nt][1] + b1));
-            const uint32_t hi = pack_bf16(gelu(acc[nt][2] + b0), gelu(acc[nt][3] + b1));
-            *reinterpret_cast<uint32_t*>(&s.act[cur ^ 1][row0 + g][c]) = lo;
-            *reinterpret_cast<uint32_t*>(&s.act[cur ^ 1][row0 + g + 8][c]) = hi;
+            *reinterpret_cast<float2*>(&s.act[cur ^ 1][row0 + g][c]) =
+                make_float2(gelu(acc[nt][0] + b0), gelu(acc[nt][1] + b1));
+            *reinterpret_cast<float2*>(&s.act[cur ^ 1][row0 + g + 8][c]) =
+                make_float2(gelu(acc[nt][2] + b0), gelu(acc[nt][3] + b1));
         }
         __syncwarp();
         cur ^= 1;
@@ -295,12 +331,10 @@ __global__ void __launch_bounds__(128) mlp_infer_bf16_kernel(const float* __rest
     // output layer: N = 8 (4 used)
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int ks = 0; ks < kHid / 16; ++ks) {
-        uint32_t a[4], b[2];
-        load_a_frag(&s.act[cur][0][0], kActStride, row0, ks * 16, lane, a);
-        load_b_frag(&s.w4[0][0], kWStride, 0, ks * 16, lane, b);
-        mma_bf16(acc, a, b);
+        uint32_t ah[4], al[4];
+        load_a_frag(&s.act[cur][0][0], row0, ks * 16, lane, ah, al);
+        mma_tile<kSplit>(acc, ah, al, &s.w4[0][0][0], &s.w4[1][0][0], kWStride, 0, ks * 16, lane);
     }
-    const int g = lane >> 2, t = lane & 3;
     for (int half = 0; half < 2; ++half) {
         const int r = row0 + g + half * 8;
         for (int j = 0; j < 2; ++j) {
@@ -324,19 +358,25 @@ __global__ void destandardise_kernel(const float* __restrict__ Zn, int n, const 
     }
 }
 
+// FP32 parameters -> BF16 hi and lo weight blocks (zero padded) and FP32 biases
 __global__ void pack_weights_kernel(const float* __restrict__ P, __nv_bfloat16* __restrict__ wpack,
                                     float* __restrict__ bpack) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    for (int i = tid; i < kHid * kInPad; i += stride) {
-        const int o = i / kInPad, k = i % kInPad;
-        wpack[i] = __float2bfloat16_rn(k < kIn ? P[woff(0) + o * kIn + k] : 0.0f);
-    }
-    for (int l = 0; l < 2; ++l)
-        for (int i = tid; i < kHid * kHid; i += stride)
-            wpack[kHid * kInPad + l * kHid * kHid + i] = __float2bfloat16_rn(P[woff(l + 1) + i]);
-    for (int i = tid; i < 8 * kHid; i += stride) {
-        const int o = i / kHid, k = i % kHid;
-        wpack[kHid * kInPad + 2 * kHid * kHid + i] = __float2bfloat16_rn(o < kOut ? P[woff(3) + o * kHid + k] : 0.0f);
+    for (int i = tid; i < kPackHalf; i += stride) {
+        float w = 0.0f;
+        if (i < kHid * kInPad) {
+            const int o = i / kInPad, k = i % kInPad;
+            w = k < kIn ? P[woff(0) + o * kIn + k] : 0.0f;
+        } else if (i < kHid * kInPad + 2 * kHid * kHid) {
+            const int j = i - kHid * kInPad, l = j / (kHid * kHid);
+            w = P[woff(l + 1) + j % (kHid * kHid)];
+        } else {
+            const int j = i - kHid * kInPad - 2 * kHid * kHid, o = j / kHid, k = j % kHid;
+            w = o < kOut ? P[woff(3) + o * kHid + k] : 0.0f;
+        }
+        const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+        wpack[i] = hi;
+        wpack[kPackHalf + i] = __float2bfloat16_rn(w - __bfloat162float(hi));
     }
     for (int i = tid; i < 3 * kHid; i += stride) bpack[i] = P[boff(i / kHid) + i % kHid];
     for (int i = tid; i < 8; i += stride) bpack[3 * kHid + i] = i < kOut ? P[boff(3) + i] : 0.0f;
@@ -431,10 +471,12 @@ int forward(lbm_surrogate* m, int n) {
     return LBM_OK;
 }
 
-// backward pass of the MSE loss against d_Yn: fills d_grad and *loss (device)
-int backward(lbm_surrogate* m, int n) {
+// backward pass of the MSE loss against d_Yn (n_valid finite targets): fills d_grad and
+// *loss (device)
+int backward(lbm_surrogate* m, int n, long long n_valid) {
     MCK(cudaMemsetAsync(m->d_loss, 0, sizeof(float), m->stream));
-    mse_kernel<<<64, 256, 0, m->stream>>>(m->d_Z[kLayers - 1], m->d_Yn, m->d_dZ[kLayers - 1], n * kOut, m->d_loss);
+    mse_kernel<<<64, 256, 0, m->stream>>>(m->d_Z[kLayers - 1], m->d_Yn, m->d_dZ[kLayers - 1], n * kOut,
+                                          (float)(1.0 / (double)n_valid), m->d_loss);
     for (int l = kLayers - 1; l >= 0; --l) {
         const int din = kDims[l], dout = kDims[l + 1];
         const float* Ain = l == 0 ? m->d_Xn : m->d_A[l - 1];
@@ -454,6 +496,16 @@ int backward(lbm_surrogate* m, int n) {
     }
     MCK(cudaGetLastError());
     return LBM_OK;
+}
+
+// finite target entries (each set needs a finite rho_v > 0; other outputs may be NaN = missing)
+long long valid_targets(const float* Y, int n) {
+    long long c = 0;
+    for (long long i = 0; i < (long long)n * kOut; ++i) {
+        if (i % kOut == 1 && !(Y[i] > 0.0f && std::isfinite(Y[i]))) return -1;
+        c += std::isfinite(Y[i]) ? 1 : 0;
+    }
+    return c;
 }
 
 int upload_inputs(lbm_surrogate* m, const float* X, const float* Y, int n) {
@@ -507,7 +559,7 @@ extern "C" int lbm_surrogate_create(const float* stats16, unsigned seed, lbm_sur
         if ((e = cudaMalloc(b, sizeof(float) * kNumParams)) != cudaSuccess) return fail(mfail(e, "cudaMalloc(params)"));
     if ((e = cudaMalloc(&m->d_stats, sizeof(float) * 16)) != cudaSuccess ||
         (e = cudaMalloc(&m->d_loss, sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_wpack, sizeof(__nv_bfloat16) * (kHid * kInPad + 2 * kHid * kHid + 8 * kHid))) !=
+        (e = cudaMalloc(&m->d_wpack, sizeof(__nv_bfloat16) * 2 * kPackHalf)) !=
             cudaSuccess ||
         (e = cudaMalloc(&m->d_bpack, sizeof(float) * (3 * kHid + 8))) != cudaSuccess)
         return fail(mfail(e, "cudaMalloc"));
@@ -545,9 +597,11 @@ extern "C" int lbm_surrogate_get_params(lbm_surrogate* m, float* params) {
 extern "C" int lbm_surrogate_loss_grad(lbm_surrogate* m, const float* X, const float* Y, int n, float* loss,
                                        float* grad) {
     if (!m || !X || !Y || n < 1) return LBM_ERR_ARG;
+    const long long nv = valid_targets(Y, n);
+    if (nv < 1) return LBM_ERR_ARG;
     int rc = upload_inputs(m, X, Y, n);
     if (!rc) rc = forward(m, n);
-    if (!rc) rc = backward(m, n);
+    if (!rc) rc = backward(m, n, nv);
     if (rc) return rc;
     if (loss) MCK(cudaMemcpyAsync(loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
     if (grad) MCK(cudaMemcpyAsync(grad, m->d_grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, m->stream));
@@ -558,6 +612,8 @@ extern "C" int lbm_surrogate_loss_grad(lbm_surrogate* m, const float* X, const f
 extern "C" int lbm_surrogate_train(lbm_surrogate* m, const float* X, const float* Y, int n,
                                    const lbm_train_cfg* cfg, float* final_loss) {
     if (!m || !X || !Y || n < 1 || !cfg || cfg->iterations < 0 || !(cfg->lr > 0)) return LBM_ERR_ARG;
+    const long long nv = valid_targets(Y, n);
+    if (nv < 1) return LBM_ERR_ARG;
     int rc = upload_inputs(m, X, Y, n);
     if (rc) return rc;
     // one iteration = full-batch forward, backward and Adam update; captured once as a graph
@@ -565,7 +621,7 @@ extern "C" int lbm_surrogate_train(lbm_surrogate* m, const float* X, const float
     cudaGraphExec_t ge = nullptr;
     MCK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
     rc = forward(m, n);
-    if (!rc) rc = backward(m, n);
+    if (!rc) rc = backward(m, n, nv);
     cudaError_t e = cudaStreamEndCapture(m->stream, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
@@ -607,23 +663,30 @@ extern "C" int lbm_surrogate_predict_fp32(lbm_surrogate* m, const float* X, int 
     return LBM_OK;
 }
 
-extern "C" int lbm_surrogate_predict_device(lbm_surrogate* m, const float* X_dev, int n, float* Y_dev, void* stream) {
-    if (!m || !X_dev || !Y_dev || n < 1) return LBM_ERR_ARG;
+extern "C" int lbm_surrogate_predict_device(lbm_surrogate* m, const float* X_dev, int n, float* Y_dev, int mode,
+                                            void* stream) {
+    if (!m || !X_dev || !Y_dev || n < 1 || (mode != LBM_INFER_SPLIT_BF16 && mode != LBM_INFER_BF16)) return LBM_ERR_ARG;
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : m->stream;
     pack_weights_kernel<<<64, 256, 0, s>>>(m->d_params, m->d_wpack, m->d_bpack);
     const int smem = (int)sizeof(InferSmem);
-    MCK(cudaFuncSetAttribute(mlp_infer_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    mlp_infer_bf16_kernel<<<(n + kQ - 1) / kQ, 128, smem, s>>>(X_dev, n, m->d_wpack, m->d_bpack, m->d_stats, Y_dev);
+    const int grid = (n + kQ - 1) / kQ;
+    if (mode == LBM_INFER_SPLIT_BF16) {
+        MCK(cudaFuncSetAttribute(mlp_infer_bf16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        mlp_infer_bf16_kernel<true><<<grid, 128, smem, s>>>(X_dev, n, m->d_wpack, m->d_bpack, m->d_stats, Y_dev);
+    } else {
+        MCK(cudaFuncSetAttribute(mlp_infer_bf16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        mlp_infer_bf16_kernel<false><<<grid, 128, smem, s>>>(X_dev, n, m->d_wpack, m->d_bpack, m->d_stats, Y_dev);
+    }
     MCK(cudaGetLastError());
     return LBM_OK;
 }
 
-extern "C" int lbm_surrogate_predict(lbm_surrogate* m, const float* X, int n, float* Y) {
+extern "C" int lbm_surrogate_predict(lbm_surrogate* m, const float* X, int n, float* Y, int mode) {
     if (!m || !X || !Y || n < 1) return LBM_ERR_ARG;
     int rc = alloc_rows(m, n);
     if (rc) return rc;
     MCK(cudaMemcpyAsync(m->d_X, X, sizeof(float) * n * kIn, cudaMemcpyHostToDevice, m->stream));
-    rc = lbm_surrogate_predict_device(m, m->d_X, n, m->d_out, m->stream);
+    rc = lbm_surrogate_predict_device(m, m->d_X, n, m->d_out, mode, m->stream);
     if (rc) return rc;
     MCK(cudaMemcpyAsync(Y, m->d_out, sizeof(float) * n * kOut, cudaMemcpyDeviceToHost, m->stream));
     MCK(cudaStreamSynchronize(m->stream));

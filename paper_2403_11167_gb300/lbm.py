@@ -144,8 +144,8 @@ def _lib():
             "lbm_surrogate_get_params": ([vp, fp], ctypes.c_int),
             "lbm_surrogate_loss_grad": ([vp, fp, fp, ctypes.c_int, fp, fp], ctypes.c_int),
             "lbm_surrogate_train": ([vp, fp, fp, ctypes.c_int, ctypes.POINTER(lbm_train_cfg), fp], ctypes.c_int),
-            "lbm_surrogate_predict": ([vp, fp, ctypes.c_int, fp], ctypes.c_int),
-            "lbm_surrogate_predict_device": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+            "lbm_surrogate_predict": ([vp, fp, ctypes.c_int, fp, ctypes.c_int], ctypes.c_int),
+            "lbm_surrogate_predict_device": ([vp, vp, ctypes.c_int, vp, ctypes.c_int, vp], ctypes.c_int),
             "lbm_surrogate_predict_fp32": ([vp, fp, ctypes.c_int, fp], ctypes.c_int),
             "lbm_surrogate_destroy": ([vp], None),
             "lbm_surrogate_last_error": ([], ctypes.c_char_p),
@@ -408,6 +408,8 @@ def _f32(a, cols=4):
 
 
 SURROGATE_INPUTS = ("Tr", "a", "b", "kappa_P")
+LBM_INFER_SPLIT_BF16 = 0
+LBM_INFER_BF16 = 1
 SURROGATE_OUTPUTS = ("rho_l", "rho_v", "width", "sigma")
 
 
@@ -424,15 +426,17 @@ class Surrogate:
         self.n_params = _lib().lbm_surrogate_num_params()
 
     @staticmethod
-    def standardisation(X, Y):
-        """stats16 of a training set: mean/std of X and of (rho_l, ln rho_v, W, sigma)."""
+    def standardisation(X, Y, weights=(1.0, 1.0, 1.0, 1.0)):
+        """stats16 of a training set: mean/std of X and of (rho_l, ln rho_v, W, sigma).  An
+        output's scale is its std / sqrt(weight), so the MSE weighs it by ``weight``."""
         X = np.asarray(X, dtype=np.float64)
         Yp = np.array(Y, dtype=np.float64)
         Yp[:, 1] = np.log(Yp[:, 1])
-        sx, sy = X.std(0), Yp.std(0)
+        sx, sy = X.std(0), np.nanstd(Yp, 0)
         sx[sx == 0] = 1.0
         sy[sy == 0] = 1.0
-        return np.concatenate([X.mean(0), sx, Yp.mean(0), sy]).astype(np.float32)
+        sy = sy / np.sqrt(np.asarray(weights, dtype=np.float64))
+        return np.concatenate([X.mean(0), sx, np.nanmean(Yp, 0), sy]).astype(np.float32)
 
     def stats(self):
         st = np.zeros(16, np.float32)
@@ -466,10 +470,12 @@ class Surrogate:
                "lbm_surrogate_train")
         return float(loss[0])
 
-    def predict(self, X):
+    def predict(self, X, mode=None):
+        """Tensor-core inference (default: split-BF16 operands, FP32 accumulation)."""
         X = _f32(X)
         Y = np.zeros_like(X)
-        _check(_lib().lbm_surrogate_predict(self.h, _fptr(X), len(X), _fptr(Y)), "lbm_surrogate_predict")
+        mode = LBM_INFER_SPLIT_BF16 if mode is None else mode
+        _check(_lib().lbm_surrogate_predict(self.h, _fptr(X), len(X), _fptr(Y), mode), "lbm_surrogate_predict")
         return Y
 
     def predict_fp32(self, X):
@@ -478,10 +484,11 @@ class Surrogate:
         _check(_lib().lbm_surrogate_predict_fp32(self.h, _fptr(X), len(X), _fptr(Y)), "lbm_surrogate_predict_fp32")
         return Y
 
-    def predict_device(self, X_dev, Y_dev, stream=None):
-        """BF16 inference on device tensors (float32, n x 4, contiguous); asynchronous."""
+    def predict_device(self, X_dev, Y_dev, stream=None, mode=None):
+        """Inference on device tensors (float32, n x 4, contiguous); asynchronous."""
+        mode = LBM_INFER_SPLIT_BF16 if mode is None else mode
         _check(_lib().lbm_surrogate_predict_device(self.h, X_dev.data_ptr(), X_dev.shape[0], Y_dev.data_ptr(),
-                                                   stream), "lbm_surrogate_predict_device")
+                                                   mode, stream), "lbm_surrogate_predict_device")
 
     def close(self):
         if getattr(self, "h", None):

@@ -181,3 +181,20 @@ def test_bf16_bound_is_first_order_and_covers_emulation():
     err = np.abs(a - exact)
     assert np.all(err <= bound)
     assert np.max(err) > 0
+
+
+def test_missing_targets_drop_out_of_loss_and_gradient():
+    """A NaN target contributes nothing: the loss over a set with missing sigma equals the
+    loss over the same set with sigma replaced by the prediction, rescaled by the count."""
+    th = _theta(14)
+    X, Y = _data(9, seed=15)
+    st = _stats(X, Y)
+    P = M.predict(th, X, st)
+    Ym = Y.copy()
+    Ym[[1, 4, 7], 3] = np.nan
+    Yf = Y.copy()
+    Yf[[1, 4, 7], 3] = P[[1, 4, 7], 3]
+    lm, gm = M.loss_grad(th, X, Ym, st)
+    lf, gf = M.loss_grad(th, X, Yf, st)
+    assert abs(lm * (36 - 3) - lf * 36) < 1e-12 * lf * 36
+    assert np.max(np.abs(gm * (36 - 3) - gf * 36)) < 1e-10 * np.max(np.abs(gf * 36))
