@@ -301,10 +301,16 @@ def run_surrogate(args):
     }
 
 
+KERNEL_SOURCES = ("lbm_kernels.cuh", "step_tma.cuh")
+
+
 def kernel_source_hash():
+    """First 12 hex digits of the SHA-256 of the step kernels' sources (per-cell arithmetic and
+    the TMA strip pipeline), concatenated in KERNEL_SOURCES order."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2403_11167_gb300", "csrc", "lbm_kernels.cuh"), "rb") as fh:
-        h.update(fh.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2403_11167_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:12]
 
 
