@@ -404,25 +404,38 @@ int autotune(lbm_batch* b) {
             auto it = g_tune_cache.find(key);
             if (it != g_tune_cache.end()) choice = it->second;
         }
+        if (const char* e = std::getenv("LBM_BATCH_ROWS")) choice = std::max(1, std::atoi(e));  // tuning experiments
         if (choice < 0) {
-            double best = 1e30;
-            for (int rows : {16, 32, 64}) {
-                build_items(b, rows);
-                int rc = upload_tables(b);
-                if (rc) return rc;
-                const double ms = time_ms(b->s_tile, [&] {
-                    for (int k = 0; k < 8; ++k) {
-                        int r = launch_tiled_step(b, k, b->s_tile);
-                        if (r) return r;
-                    }
-                    return (int)LBM_OK;
-                }, &rc);
-                if (rc) return rc;
-                if (ms < best) {
-                    best = ms;
-                    choice = rows;
+            // two passes in opposite orders, 16 steps per trial, best time per candidate:
+            // a single short pass in one order favoured whichever candidate ran last
+            const int cand[3] = {16, 32, 64};
+            double best_ms[3] = {1e30, 1e30, 1e30};
+            for (int pass = 0; pass < 2; ++pass)
+                for (int j = 0; j < 3; ++j) {
+                    const int c = pass == 0 ? j : 2 - j;
+                    build_items(b, cand[c]);
+                    int rc = upload_tables(b);
+                    if (rc) return rc;
+                    const double ms = time_ms(b->s_tile, [&] {
+                        for (int k = 0; k < 16; ++k) {
+                            int r = launch_tiled_step(b, k, b->s_tile);
+                            if (r) return r;
+                        }
+                        return (int)LBM_OK;
+                    }, &rc);
+                    if (rc) return rc;
+                    best_ms[c] = std::min(best_ms[c], ms);
                 }
-            }
+            // the trial sees every lattice active; later, only the longest lattices remain and
+            // more (shorter) strips keep the GPU busy: take the shortest strips within 5% of the
+            // best trial time
+            double best = 1e30;
+            for (int c = 0; c < 3; ++c) best = std::min(best, best_ms[c]);
+            for (int c = 0; c < 3; ++c)
+                if (best_ms[c] <= 1.05 * best) {
+                    choice = cand[c];
+                    break;
+                }
             std::lock_guard<std::mutex> g(g_tune_mu);
             g_tune_cache[key] = choice;
         }

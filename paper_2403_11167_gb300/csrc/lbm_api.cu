@@ -16,6 +16,7 @@
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
 #include "step_tma.cuh"
+#include "step_warp.cuh"
 #include "thermo.h"
 
 namespace {
@@ -44,6 +45,18 @@ constexpr int kTXd = 64;   // columns per CTA, FP64
 constexpr int kGraphSteps = 64;
 constexpr int kRedBlocks = 304;  // observables partial-reduction blocks (2 x 152 SMs)
 constexpr int kTmaStages = LBM_TMA_STAGES;  // row-pipeline depth of the TMA-fed FP32 kernels
+// Pseudopotential FP32 step: warp-independent windows (1) or CTA-synchronised strips (0).
+#ifndef LBM_PP_WARP
+#define LBM_PP_WARP 1
+#endif
+#ifndef LBM_PPW_STAGES
+#define LBM_PPW_STAGES 6
+#endif
+constexpr bool kPPWarp = LBM_PP_WARP != 0;
+constexpr int kPPWarps = 8;                    // consumer warps per CTA
+constexpr int kPPWStages = LBM_PPW_STAGES;
+using PPWSmem = lbmk::WarpStripSmem<kPPWarps, kPPWStages, 30>;
+constexpr int kPPWTX = PPWSmem::TX;            // widest strip (240 columns)
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
@@ -274,19 +287,23 @@ static void fill_step_params(lbmk::StepParams<real>& s, const lbm_ctx* c) {
     s.fy = (real)p.body_fy;
 }
 
-static int choose_rows(int nx, int ny, int tx) {
+static int choose_rows(int nx, int ny, int tx, int strips_per_sm) {
     // Enough CTAs to fill 152 SMs several times over, but long strips so the y halo
     // (recomputed rows) stays a few percent.  LBM_ROWS overrides (tuning experiments).
     if (const char* e = std::getenv("LBM_ROWS")) {
         const int r = std::atoi(e);
         if (r >= 1) return r < ny ? r : ny;
     }
-    // About 14 strips per SM: several waves of CTAs, so the last partial wave is a small
-    // fraction of the launch (measured: 32-row strips beat 64-row ones by 8-10% at 4096^2).
+    // Measured at 4096^2 (three CTAs per SM): the pseudopotential kernel is flat from 20 to
+    // 36 rows, the free-energy kernel (5 halo rows per strip) best at 36-40; below 16 rows
+    // the halo dominates (2048^2).
     const long long gx = (nx + tx - 1) / tx;
-    const long long target = 152LL * 14;
+    const long long target = 152LL * strips_per_sm;
     long long rows = (ny * gx + target - 1) / target;
     if (rows < 8) rows = 8;
+    // at least 16 rows while that still gives a full wave of CTAs (3 per SM); small lattices
+    // keep shorter strips so that they still spread over the GPU
+    if (rows < 16 && gx * ((ny + 15) / 16) >= 152LL * 3) rows = 16;
     if (rows > 64) rows = 64;
     if (rows > ny) rows = ny;
     return (int)rows;
@@ -310,7 +327,11 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->prec = c->prm.precision;
     c->esz = c->prec == LBM_F64 ? 8 : 4;
     c->pitch = plane_pitch(nx, ny);
-    c->rows = choose_rows(nx, ny, c->prec == LBM_F64 ? kTXd : kTXf);
+    {
+        const bool ppm = p->model == LBM_PSEUDOPOTENTIAL;
+        const int tx = c->prec == LBM_F64 ? kTXd : (kPPWarp && ppm ? kPPWTX : kTXf);
+        c->rows = choose_rows(nx, ny, tx, ppm ? 16 : 12);
+    }
     const size_t need = lbm_workspace_bytes(c->prec, nx, ny);
     if (workspace) {
         if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
@@ -370,9 +391,12 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
         cudaError_t e2 = cudaFuncSetAttribute(lbmk::fe_step_tma<kTXf, kTmaStages>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)sizeof(lbmk::FETmaSmem<kTXf, kTmaStages>));
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaError_t e3 = cudaFuncSetAttribute(lbmk::pp_step_warp<kPPWarps, kPPWStages>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPWSmem));
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
             lbm_destroy(c);
-            return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaFuncSetAttribute(max dynamic smem)");
+            return cuda_fail(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3,
+                             "cudaFuncSetAttribute(max dynamic smem)");
         }
     }
     *out = c;
@@ -406,7 +430,11 @@ static int launch_step(lbm_ctx* c, int src) {
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
-    if (c->use_tma) {
+    if (c->use_tma && pp && kPPWarp) {
+        dim3 grid((c->nx + kPPWTX - 1) / kPPWTX, (c->ny + c->rows - 1) / c->rows);
+        lbmk::pp_step_warp<kPPWarps, kPPWStages><<<grid, (kPPWarps + 1) * 32, sizeof(PPWSmem), c->stream>>>(
+            (const float*)fin, (float*)fout, c->spf, c->d_err);
+    } else if (c->use_tma) {
         dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
         if (pp)
             lbmk::pp_step_tma<kTXf, kTmaStages>

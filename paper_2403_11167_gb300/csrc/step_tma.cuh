@@ -180,6 +180,14 @@ __device__ __forceinline__ int next_stage(int s, int S) { return s + 1 == S ? 0 
 #ifndef LBM_FE_MINB
 #define LBM_FE_MINB 1
 #endif
+#ifndef LBM_PP_UNROLL
+#define LBM_PP_UNROLL 1
+#endif
+#ifndef LBM_FE_UNROLL
+#define LBM_FE_UNROLL 1
+#endif
+constexpr int kPPUnroll = LBM_PP_UNROLL;  // row-loop unroll factors
+constexpr int kFEUnroll = LBM_FE_UNROLL;
 
 // One CTA's strip of the pseudopotential step: columns [x0, x0 + w), rows [y0, y1).
 template <int TX, int S>
@@ -223,7 +231,7 @@ __device__ __forceinline__ void pp_strip_tma(const float* __restrict__ fin, floa
     bool failed = __syncthreads_or(!(mbar_wait_bounded(&sm.bar[0], 0) && mbar_wait_bounded(&sm.bar[1], 0)));
     int sm2 = 0, sm1 = 1, s0 = 2 % S;  // stages of rows q-1, q, q+1
     uint32_t par = 0;                  // parity of the fill being waited for (stage s0)
-#pragma unroll 1
+#pragma unroll(kPPUnroll)
     for (int q = y0 - 1; q <= y1 && !failed; ++q) {
         const int k = q + 1 - rbase;  // staged index of row q+1
         const bool ok = mbar_wait_bounded(&sm.bar[s0], par);
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(TX + 32, LBM_FE_MINB) fe_step_tma(const float*
     bool failed = __syncthreads_or(!(mbar_wait_bounded(&sm.bar[0], 0) && mbar_wait_bounded(&sm.bar[1], 0)));
     int sm2 = 0, sm1 = 1, s0 = 2 % S;
     uint32_t par = 0;
-#pragma unroll 1
+#pragma unroll(kFEUnroll)
     for (int q = y0 - 2; q <= y1 + 2 && !failed; ++q) {
         const int k = q + 1 - rbase;
         const bool load = q <= y1 + 1;  // rho rows run to y1+1; the last iteration only finishes mu and collides

@@ -237,11 +237,12 @@ def test_divergence_is_reported_not_crashed():
 
 
 @pytest.mark.parametrize("model", [PP, FE])
-@pytest.mark.parametrize("shape", [(8, 4), (300, 200), (132, 7), (1024, 70)])
+@pytest.mark.parametrize("shape", [(8, 4), (300, 200), (132, 7), (1024, 70), (244, 9), (484, 33), (4100, 6)])
 def test_tma_pipeline_matches_direct_kernel(model, shape, monkeypatch):
-    """The TMA-fed FP32 kernels (row pipeline through shared memory) and the direct-load
-    kernels run the same per-cell arithmetic: on lattices with nx % 4 == 0 (single tile,
-    ragged tiles, thin strips) their populations agree bitwise after 50 steps."""
+    """The TMA-fed FP32 kernels (row pipeline through shared memory; for the pseudopotential
+    model the warp-window kernel) and the direct-load kernels run the same per-cell
+    arithmetic: on lattices with nx % 4 == 0 (single tile, ragged and uneven strips, thin
+    strips, a 4-column last strip) their populations agree after 50 steps."""
     nx, ny = shape
     a, rp, th = gpu_context(model, F32, nx, ny, Tr=0.85, tau_nu=0.8)
     monkeypatch.setenv("LBM_NO_TMA", "1")
