@@ -17,6 +17,7 @@
 #include "lbm_kernels.cuh"
 #include "step_tma.cuh"
 #include "step_warp.cuh"
+#include "step_pair.cuh"
 #include "thermo.h"
 
 namespace {
@@ -57,6 +58,18 @@ constexpr int kPPWarps = 8;                    // consumer warps per CTA
 constexpr int kPPWStages = LBM_PPW_STAGES;
 using PPWSmem = lbmk::WarpStripSmem<kPPWarps, kPPWStages, 30>;
 constexpr int kPPWTX = PPWSmem::TX;            // widest strip (240 columns)
+// Free-energy FP32 step: two cells per lane in warp windows (1) or CTA-synchronised strips (0).
+#ifndef LBM_FE_PAIR
+#define LBM_FE_PAIR 1
+#endif
+#ifndef LBM_FEP_STAGES
+#define LBM_FEP_STAGES 8
+#endif
+constexpr bool kFEPair = LBM_FE_PAIR != 0;
+constexpr int kFEPWarps = 4;                   // consumer warps per CTA
+constexpr int kFEPStages = LBM_FEP_STAGES;     // >= 5: a warp reads rows q-3 .. q+1
+using FEPSmem = lbmk::WarpStripSmem<kFEPWarps, kFEPStages, 60>;
+constexpr int kFEPTX = FEPSmem::TX;            // widest strip (240 columns)
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
@@ -329,7 +342,7 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->pitch = plane_pitch(nx, ny);
     {
         const bool ppm = p->model == LBM_PSEUDOPOTENTIAL;
-        const int tx = c->prec == LBM_F64 ? kTXd : (kPPWarp && ppm ? kPPWTX : kTXf);
+        const int tx = c->prec == LBM_F64 ? kTXd : ppm ? (kPPWarp ? kPPWTX : kTXf) : (kFEPair ? kFEPTX : kTXf);
         c->rows = choose_rows(nx, ny, tx, ppm ? 16 : 12);
     }
     const size_t need = lbm_workspace_bytes(c->prec, nx, ny);
@@ -393,9 +406,11 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
                                               (int)sizeof(lbmk::FETmaSmem<kTXf, kTmaStages>));
         cudaError_t e3 = cudaFuncSetAttribute(lbmk::pp_step_warp<kPPWarps, kPPWStages>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPWSmem));
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        cudaError_t e4 = cudaFuncSetAttribute(lbmk::fe_step_pair<kFEPWarps, kFEPStages>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FEPSmem));
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
             lbm_destroy(c);
-            return cuda_fail(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3,
+            return cuda_fail(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4,
                              "cudaFuncSetAttribute(max dynamic smem)");
         }
     }
@@ -433,6 +448,10 @@ static int launch_step(lbm_ctx* c, int src) {
     if (c->use_tma && pp && kPPWarp) {
         dim3 grid((c->nx + kPPWTX - 1) / kPPWTX, (c->ny + c->rows - 1) / c->rows);
         lbmk::pp_step_warp<kPPWarps, kPPWStages><<<grid, (kPPWarps + 1) * 32, sizeof(PPWSmem), c->stream>>>(
+            (const float*)fin, (float*)fout, c->spf, c->d_err);
+    } else if (c->use_tma && !pp && kFEPair) {
+        dim3 grid((c->nx + kFEPTX - 1) / kFEPTX, (c->ny + c->rows - 1) / c->rows);
+        lbmk::fe_step_pair<kFEPWarps, kFEPStages><<<grid, (kFEPWarps + 1) * 32, sizeof(FEPSmem), c->stream>>>(
             (const float*)fin, (float*)fout, c->spf, c->d_err);
     } else if (c->use_tma) {
         dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);

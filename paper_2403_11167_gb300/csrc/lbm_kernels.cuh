@@ -260,6 +260,155 @@ __device__ __forceinline__ real fe_mu(real rc, const real rn[9], const StepParam
 }
 
 // ---------------------------------------------------------------------------------
+// FP32 free-energy arithmetic, written once for one cell (F1) or two cells at a time (F2,
+// Blackwell's packed FP32: one instruction computes both lanes).  Every operation is an
+// explicit correctly rounded add / multiply / fused multiply-add, never re-associated or
+// contracted by the compiler, so the single-cell and the two-cell kernels produce bitwise
+// identical cells.  The algebra is that of fe_collide / fe_mu above (Eqs. 20, 21, 24, 29).
+struct F1 {
+    float v;
+    __device__ __forceinline__ F1() {}
+    __device__ __forceinline__ explicit F1(float x) : v(x) {}
+    static __device__ __forceinline__ F1 c(float s) { return F1(s); }
+};
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1(__fadd_rn(a.v, b.v)); }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1(__fsub_rn(a.v, b.v)); }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1(__fmul_rn(a.v, b.v)); }
+__device__ __forceinline__ F1 operator-(F1 a) { return F1(-a.v); }
+__device__ __forceinline__ F1 fmav(F1 a, F1 b, F1 c) { return F1(__fmaf_rn(a.v, b.v, c.v)); }
+
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ explicit F2(float2 x) : v(x) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    static __device__ __forceinline__ F2 c(float s) { return F2(s, s); }
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__fadd2_rn(a.v, (-b).v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 fmav(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
+// Eq. (29) relative to the coexistence reference (see mu_bulk_rel), one cell, explicit ops.
+__device__ __forceinline__ float mu_bulk_f1(float rho, const StepParams<float>& P) {
+    const bool liq = rho >= P.rho_split;
+    const float rr = liq ? P.rho_ref_l : P.rho_ref_v;
+    const float ur = liq ? P.ur_l : P.ur_v;
+    const float ur3 = liq ? P.ur3_l : P.ur3_v;
+    const float irr = liq ? P.irr_l : P.irr_v;
+    const F1 d = F1(rho) - F1(rr);
+    const F1 u = fmav(F1(-P.b4), F1(rho), F1(1.0f));
+    const F1 U(ur);
+    const F1 num = fmav(F1(2.0f), fmav(U, U, fmav(U, u, u * u)), (U + u) * u * U);
+    const F1 dg = F1(P.b4) * d * num * F1(__frcp_rn((u * u * u * F1(ur3)).v));
+    const F1 lg(log1pf((d * F1(irr)).v));
+    return (fmav(F1(P.RT), dg + lg, F1(-2.0f * P.a) * d) + F1(liq ? P.mu_off_l : 0.0f)).v;
+}
+__device__ __forceinline__ F1 mu_bulk_v(F1 rho, const StepParams<float>& P) { return F1(mu_bulk_f1(rho.v, P)); }
+__device__ __forceinline__ F2 mu_bulk_v(F2 rho, const StepParams<float>& P) {
+    return F2(mu_bulk_f1(rho.v.x, P), mu_bulk_f1(rho.v.y, P));
+}
+__device__ __forceinline__ F1 rcp_v(F1 x) { return F1(__frcp_rn(x.v)); }
+__device__ __forceinline__ F2 rcp_v(F2 x) { return F2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
+
+template <class F>
+__device__ __forceinline__ F sum9_v(const F v[9]) {
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
+// mu at the cell from rho at the cell (rc) and at x + c_i (rn[1..8]).
+template <class F>
+__device__ __forceinline__ F fe_mu_v(F rc, const F rn[9], const StepParams<float>& P) {
+    const F lap = fmav((rn[1] - rc) + (rn[2] - rc) + ((rn[3] - rc) + (rn[4] - rc)), F::c(2.0f / 3.0f),
+                       ((rn[5] - rc) + (rn[6] - rc) + ((rn[7] - rc) + (rn[8] - rc))) * F::c(1.0f / 6.0f));
+    return fmav(F::c(-P.kappa), lap, mu_bulk_v(rc, P));
+}
+
+template <class F>
+__device__ __forceinline__ void apply_dm_v(F v[9], F de, F dz, F djx, F dqx, F djy, F dqy, F dpxx, F dpxy) {
+    const F A = fmav(de, F::c(-1.0f / 36.0f), dz * F::c(-1.0f / 18.0f));
+    const F B = fmav(de, F::c(1.0f / 18.0f), dz * F::c(1.0f / 36.0f));
+    const F X1 = (djx - dqx) * F::c(1.0f / 6.0f);
+    const F Y1 = (djy - dqy) * F::c(1.0f / 6.0f);
+    const F X2 = fmav(djx, F::c(1.0f / 6.0f), dqx * F::c(1.0f / 12.0f));
+    const F Y2 = fmav(djy, F::c(1.0f / 6.0f), dqy * F::c(1.0f / 12.0f));
+    const F Pp = dpxx * F::c(0.25f);
+    const F Z = dpxy * F::c(0.25f);
+    v[0] = fmav(dz - de, F::c(1.0f / 9.0f), v[0]);
+    v[1] = v[1] + ((A + X1) + Pp);
+    v[2] = v[2] + ((A + Y1) - Pp);
+    v[3] = v[3] + ((A - X1) + Pp);
+    v[4] = v[4] + ((A - Y1) - Pp);
+    v[5] = v[5] + (((B + X2) + Y2) + Z);
+    v[6] = v[6] + (((B - X2) + Y2) - Z);
+    v[7] = v[7] + (((B - X2) - Y2) + Z);
+    v[8] = v[8] + (((B + X2) - Y2) - Z);
+}
+
+// Improved well-balanced free-energy collision (Eqs. 1, 6, 20, 21, 24); mn, rn: mu and rho
+// at x + c_i (i = 1..8).
+template <class F>
+__device__ __forceinline__ void fe_collide_v(F v[9], F rho, const F mn[9], const F rn[9],
+                                             const StepParams<float>& P) {
+    const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
+    const F gmx = fmav(mn[1] - mn[3], w1, ((mn[5] - mn[7]) + (mn[8] - mn[6])) * w2);
+    const F gmy = fmav(mn[2] - mn[4], w1, ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2);
+    const F grx = fmav(rn[1] - rn[3], w1, ((rn[5] - rn[7]) + (rn[8] - rn[6])) * w2);
+    const F gry = fmav(rn[2] - rn[4], w1, ((rn[5] - rn[7]) + (rn[6] - rn[8])) * w2);
+    const F Fx = fmav(-rho, gmx, F::c(P.fx)), Fy = fmav(-rho, gmy, F::c(P.fy));
+    const F jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const F jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const F inv_rho = rcp_v(rho);
+    const F ux = fmav(F::c(0.5f), Fx, jx) * inv_rho;
+    const F uy = fmav(F::c(0.5f), Fy, jy) * inv_rho;
+    const F sax = (v[1] + v[2]) + (v[3] + v[4]);
+    const F sdg = (v[5] + v[6]) + (v[7] + v[8]);
+    const F e = fmav(F::c(-4.0f), v[0], fmav(F::c(2.0f), sdg, -sax));
+    const F z = fmav(F::c(4.0f), v[0], fmav(F::c(-2.0f), sax, sdg));
+    const F qx = fmav(F::c(2.0f), v[3] - v[1], (v[5] - v[6]) + (v[8] - v[7]));
+    const F qy = fmav(F::c(2.0f), v[4] - v[2], (v[5] + v[6]) - (v[7] + v[8]));
+    const F pxx = (v[1] + v[3]) - (v[2] + v[4]);
+    const F pxy = (v[5] + v[7]) - (v[6] + v[8]);
+    const F uu = fmav(ux, ux, uy * uy);
+    const F uF = fmav(ux, Fx, uy * Fy);
+    const F s = fmav(ux, grx, uy * gry);                                      // u . grad rho
+    const F Gx = fmav(grx, F::c(1.0f / 3.0f), Fx), Gy = fmav(gry, F::c(1.0f / 3.0f), Fy);  // F + c_s^2 grad rho
+    const F fe = fmav(F::c(6.0f), uF, F::c(4.0f) * s);
+    const float he = 1.0f - 0.5f * P.s_e, hz = 1.0f - 0.5f * P.s_z, hq = 1.0f - 0.5f * P.s_q,
+                hn = 1.0f - 0.5f * P.s_nu;
+    const F de = fmav(F::c(he), fe, F::c(-P.s_e) * (e - rho * fmav(F::c(3.0f), uu, F::c(-4.0f))));
+    const F dz = fmav(F::c(-hz), fe, F::c(-P.s_z) * (z - rho * fmav(F::c(-3.0f), uu, F::c(4.0f))));
+    const F dqx = fmav(F::c(-hq), Fx, F::c(-P.s_q) * fmav(rho, ux, qx));
+    const F dqy = fmav(F::c(-hq), Fy, F::c(-P.s_q) * fmav(rho, uy, qy));
+    const F dpxx = fmav(F::c(2.0f * hn), fmav(ux, Gx, -(uy * Gy)), F::c(-P.s_nu) * (pxx - rho * fmav(ux, ux, -(uy * uy))));
+    const F dpxy = fmav(F::c(hn), fmav(ux, Gy, uy * Gx), F::c(-P.s_nu) * (pxy - rho * ux * uy));
+    apply_dm_v(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+}
+
+// FP32 single-cell entry points used by every FP32 free-energy kernel (the templates above
+// serve FP64).
+__device__ __forceinline__ void fe_collide(float v[9], float rho, const float mn[9], const float rn[9],
+                                           const StepParams<float>& P) {
+    F1 vv[9], m[9], r[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        vv[i] = F1(v[i]);
+        m[i] = F1(mn[i]);
+        r[i] = F1(rn[i]);
+    }
+    fe_collide_v(vv, F1(rho), m, r, P);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = vv[i].v;
+}
+__device__ __forceinline__ float fe_mu(float rc, const float rn[9], const StepParams<float>& P) {
+    F1 r[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r[i] = F1(rn[i]);
+    return fe_mu_v(F1(rc), r, P).v;
+}
+
+// ---------------------------------------------------------------------------------
 // Pseudopotential step.  Block = TX main threads (one column each) + one halo warp.
 template <typename real, int TX>
 __global__ void __launch_bounds__(TX + 32) pp_step_kernel(const real* __restrict__ fin, real* __restrict__ fout,

@@ -1,0 +1,165 @@
+// step_pair.cuh -- FP32 free-energy step: warp-independent windows, two cells per lane.
+//
+// Per-cell arithmetic: fe_mu_v / fe_collide_v (lbm_kernels.cuh) on F2, Blackwell's packed
+// FP32, so one instruction updates both cells of a lane; results are bitwise those of the
+// single-cell kernels.  Data movement: the TMA row ring of step_warp.cuh (one producer warp,
+// per-stage full/empty mbarriers, no CTA barrier per row).  Each consumer warp owns at most
+// 60 columns plus two halo columns on each side, two adjacent columns per lane: it keeps rho
+// of the last four rows and mu of the last three in registers, reads x-neighbours with warp
+// shuffles, and re-pulls the populations of the row it collides (two rows behind the row it
+// pulls) from the ring, which therefore holds rows q-3 .. q+1 of every warp plus prefetch.
+//
+// Iteration q of a consumer warp: pull row q (staged rows q-1..q+1), rho(q); mu(q-1) from rho
+// rows q-2..q; collide row q-2 with mu rows q-3..q-1 and rho rows q-3..q-1, re-pulling its
+// populations from staged rows q-3..q-1; release the stage of row q-3.
+//
+// Requirements (checked on the host): nx % 4 == 0, nx >= 8, ny >= 4; every wait bounded.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_kernels.cuh"
+#include "step_tma.cuh"
+#include "step_warp.cuh"
+
+namespace lbmk {
+
+// Populations of the two cells at staged columns sc, sc + 1 (sc even) pulled from the stages of
+// rows q-1 (Rm), q (R0), q+1 (Rp): v_i = f_i(x - c_i).
+template <int W8>
+__device__ __forceinline__ void pull_pair(const float* Rm, const float* R0, const float* Rp, int sc, F2 v[9]) {
+    v[0] = F2(*reinterpret_cast<const float2*>(R0 + 0 * W8 + sc));
+    v[1] = F2(R0[1 * W8 + sc - 1], R0[1 * W8 + sc]);
+    v[2] = F2(*reinterpret_cast<const float2*>(Rm + 2 * W8 + sc));
+    v[3] = F2(R0[3 * W8 + sc + 1], R0[3 * W8 + sc + 2]);
+    v[4] = F2(*reinterpret_cast<const float2*>(Rp + 4 * W8 + sc));
+    v[5] = F2(Rm[5 * W8 + sc - 1], Rm[5 * W8 + sc]);
+    v[6] = F2(Rm[6 * W8 + sc + 1], Rm[6 * W8 + sc + 2]);
+    v[7] = F2(Rp[7 * W8 + sc + 1], Rp[7 * W8 + sc + 2]);
+    v[8] = F2(Rp[8 * W8 + sc - 1], Rp[8 * W8 + sc]);
+}
+
+// A row of a field held as pairs, with the left neighbour of the first cell (L) and the right
+// neighbour of the second (R) from the adjacent lanes.
+struct Row2 {
+    F2 c;
+    float L, R;
+};
+__device__ __forceinline__ Row2 with_neighbours(F2 c) {
+    Row2 r;
+    r.c = c;
+    r.L = __shfl_up_sync(0xffffffffu, c.v.y, 1);
+    r.R = __shfl_down_sync(0xffffffffu, c.v.x, 1);
+    return r;
+}
+
+// Values at x + c_i (i = 1..8) of both cells of a lane, from the rows below (ym), at (y0) and
+// above (yp); y grows with the row index.
+__device__ __forceinline__ void neighbours_pair(const Row2& ym, const Row2& y0, const Row2& yp, F2 n[9]) {
+    n[0] = y0.c;
+    n[1] = F2(y0.c.v.y, y0.R);   // (+1, 0)
+    n[2] = yp.c;                 // ( 0, +1)
+    n[3] = F2(y0.L, y0.c.v.x);   // (-1, 0)
+    n[4] = ym.c;                 // ( 0, -1)
+    n[5] = F2(yp.c.v.y, yp.R);   // (+1, +1)
+    n[6] = F2(yp.L, yp.c.v.x);   // (-1, +1)
+    n[7] = F2(ym.L, ym.c.v.x);   // (-1, -1)
+    n[8] = F2(ym.c.v.y, ym.R);   // (+1, -1)
+}
+
+template <int NW, int S>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __restrict__ fin,
+                                                                 float* __restrict__ fout, const StepParams<float> P,
+                                                                 int* __restrict__ err) {
+    constexpr int TXW = 60;
+    using Smem = WarpStripSmem<NW, S, TXW>;
+    constexpr int W8 = Smem::W8;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    const int nx = P.nx;
+    const int wb = warp_strip_width(nx, gridDim.x);
+    const int x0 = blockIdx.x * wb;
+    const int w = min(wb, nx - x0);
+    if (w <= 0) return;
+    const int y0 = blockIdx.y * P.rows;
+    const int y1 = min(y0 + P.rows, P.ny);
+    const int rbase = y0 - 3;
+    const int nsrc = y1 - y0 + 6;  // source rows y0-3 .. y1+2 (rho rows y0-2 .. y1+1)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NW);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == NW) {  // producer warp
+        if (lane == 0) {
+            int issued = 0;
+            if (!ring_produce<S, W8>(fin, P, rbase, nsrc, x0, w, sm.stage, sm.full, sm.empty, &issued)) {
+                atomicExch(err, 1);
+                drain_stages<S>(sm.full, issued);
+            }
+        }
+        return;
+    }
+    // consumer warp: columns [cw, cw + nw) of the strip (nw even), lane l at columns
+    // cw - 2 + 2l and cw - 1 + 2l
+    const int ww = (((w + NW - 1) / NW) + 1) & ~1;
+    const int cw = warp * ww;
+    const int nw = max(0, min(ww, w - cw));
+    const int col = cw - 2 + 2 * lane;
+    const bool act = nw > 0 && 2 * lane <= nw + 2;           // rho and mu lanes
+    const bool out = act && lane >= 1 && 2 * lane <= nw;     // both cells inside the warp's run
+    const int sc = col + 4;
+    Row2 r1, r2, r3;  // rho of rows q-1, q-2, q-3
+    Row2 m2, m3;      // mu of rows q-2, q-3
+    r1.c = r2.c = r3.c = m2.c = m3.c = F2::c(1.0f);
+    r1.L = r1.R = r2.L = r2.R = r3.L = r3.R = m2.L = m2.R = m3.L = m3.R = 1.0f;
+    bool ok = mbar_wait_bounded(&sm.full[0], 0) && mbar_wait_bounded(&sm.full[1], 0);
+#pragma unroll 1
+    for (int q = y0 - 2; q <= y1 + 1 && ok; ++q) {
+        const int k = q + 1 - rbase;  // ring index of row q+1
+        ok = mbar_wait_bounded(&sm.full[k % S], (uint32_t)((k / S) & 1));
+        if (!ok) break;
+        // pull row q, rho(q)
+        F2 rho0 = F2::c(1.0f);
+        if (act) {
+            F2 v[9];
+            pull_pair<W8>(sm.stage[(k - 2) % S], sm.stage[(k - 1) % S], sm.stage[k % S], sc, v);
+            rho0 = sum9_v(v);
+        }
+        const Row2 r0 = with_neighbours(rho0);
+        // mu(q-1) from rho rows q-2, q-1, q
+        Row2 m1;
+        {
+            F2 rn[9];
+            neighbours_pair(r2, r1, r0, rn);
+            const F2 mu = (act && q >= y0) ? fe_mu_v(r1.c, rn, P) : F2::c(0.0f);
+            m1 = with_neighbours(mu);
+        }
+        // collide row q-2 (ring indices k-4 .. k-2 hold source rows q-3 .. q-1)
+        if (out && q >= y0 + 2) {
+            F2 v[9], mn[9], rn[9];
+            pull_pair<W8>(sm.stage[(k - 4) % S], sm.stage[(k - 3) % S], sm.stage[(k - 2) % S], sc, v);
+            neighbours_pair(m3, m2, m1, mn);
+            neighbours_pair(r3, r2, r1, rn);
+            fe_collide_v(v, r2.c, mn, rn, P);
+            float* o = fout + (long long)(q - 2) * nx + x0 + col;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) *reinterpret_cast<float2*>(o + i * P.pitch) = v[i].v;
+        }
+        // row q-3 (ring index k-4) is no longer read by this warp
+        __syncwarp();
+        if (lane == 0 && k >= 4) mbar_arrive(&sm.empty[(k - 4) % S]);
+        r3 = r2;
+        r2 = r1;
+        r1 = r0;
+        m3 = m2;
+        m2 = m1;
+    }
+    if (!ok) atomicExch(err, 1);
+}
+
+}  // namespace lbmk
