@@ -301,7 +301,7 @@ def run_surrogate(args):
     }
 
 
-KERNEL_SOURCES = ("lbm_kernels.cuh", "step_tma.cuh", "step_warp.cuh")
+KERNEL_SOURCES = ("lbm_kernels.cuh", "step_tma.cuh", "step_warp.cuh", "step_pair.cuh")
 
 
 def kernel_source_hash():
@@ -431,7 +431,7 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
-    names = ["pp_step_warp", "fe_step_tma"]
+    names = ["pp_step_pair", "fe_step_pair"]
     per_launch_s = [ms * 1e-3 / (args.steps * nsteps) for ms in per_model_ms]
     dom = int(np.argmax(per_model_ms))
     peak, peak_kind = measured_peak_gbs()

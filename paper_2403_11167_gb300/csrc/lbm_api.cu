@@ -58,12 +58,24 @@ constexpr int kPPWarps = 8;                    // consumer warps per CTA
 constexpr int kPPWStages = LBM_PPW_STAGES;
 using PPWSmem = lbmk::WarpStripSmem<kPPWarps, kPPWStages, 30>;
 constexpr int kPPWTX = PPWSmem::TX;            // widest strip (240 columns)
+// Pseudopotential FP32 step with two cells per lane (1; takes precedence over LBM_PP_WARP).
+#ifndef LBM_PP_PAIR
+#define LBM_PP_PAIR 1
+#endif
+#ifndef LBM_PPP_STAGES
+#define LBM_PPP_STAGES 6
+#endif
+constexpr bool kPPPair = LBM_PP_PAIR != 0;
+constexpr int kPPPWarps = 4;
+constexpr int kPPPStages = LBM_PPP_STAGES;     // >= 4: a warp reads rows q-2 .. q+1
+using PPPSmem = lbmk::WarpStripSmem<kPPPWarps, kPPPStages, 60>;
+constexpr int kPPPTX = PPPSmem::TX;
 // Free-energy FP32 step: two cells per lane in warp windows (1) or CTA-synchronised strips (0).
 #ifndef LBM_FE_PAIR
 #define LBM_FE_PAIR 1
 #endif
 #ifndef LBM_FEP_STAGES
-#define LBM_FEP_STAGES 8
+#define LBM_FEP_STAGES 6
 #endif
 constexpr bool kFEPair = LBM_FE_PAIR != 0;
 constexpr int kFEPWarps = 4;                   // consumer warps per CTA
@@ -342,7 +354,8 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->pitch = plane_pitch(nx, ny);
     {
         const bool ppm = p->model == LBM_PSEUDOPOTENTIAL;
-        const int tx = c->prec == LBM_F64 ? kTXd : ppm ? (kPPWarp ? kPPWTX : kTXf) : (kFEPair ? kFEPTX : kTXf);
+        const int tx = c->prec == LBM_F64 ? kTXd
+                       : ppm ? (kPPPair ? kPPPTX : kPPWarp ? kPPWTX : kTXf) : (kFEPair ? kFEPTX : kTXf);
         c->rows = choose_rows(nx, ny, tx, ppm ? 16 : 12);
     }
     const size_t need = lbm_workspace_bytes(c->prec, nx, ny);
@@ -408,10 +421,16 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPWSmem));
         cudaError_t e4 = cudaFuncSetAttribute(lbmk::fe_step_pair<kFEPWarps, kFEPStages>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FEPSmem));
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+        cudaError_t e5 = cudaFuncSetAttribute(lbmk::pp_step_pair<kPPPWarps, kPPPStages>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPPSmem));
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess) {
             lbm_destroy(c);
-            return cuda_fail(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4,
-                             "cudaFuncSetAttribute(max dynamic smem)");
+            const cudaError_t e = e1 != cudaSuccess   ? e1
+                                  : e2 != cudaSuccess ? e2
+                                  : e3 != cudaSuccess ? e3
+                                  : e4 != cudaSuccess ? e4
+                                                      : e5;
+            return cuda_fail(e, "cudaFuncSetAttribute(max dynamic smem)");
         }
     }
     *out = c;
@@ -445,7 +464,11 @@ static int launch_step(lbm_ctx* c, int src) {
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
-    if (c->use_tma && pp && kPPWarp) {
+    if (c->use_tma && pp && kPPPair) {
+        dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
+        lbmk::pp_step_pair<kPPPWarps, kPPPStages><<<grid, (kPPPWarps + 1) * 32, sizeof(PPPSmem), c->stream>>>(
+            (const float*)fin, (float*)fout, c->spf, c->d_err);
+    } else if (c->use_tma && pp && kPPWarp) {
         dim3 grid((c->nx + kPPWTX - 1) / kPPWTX, (c->ny + c->rows - 1) / c->rows);
         lbmk::pp_step_warp<kPPWarps, kPPWStages><<<grid, (kPPWarps + 1) * 32, sizeof(PPWSmem), c->stream>>>(
             (const float*)fin, (float*)fout, c->spf, c->d_err);

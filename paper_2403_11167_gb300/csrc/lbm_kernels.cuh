@@ -41,30 +41,11 @@ struct StepParams {
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
-// Reciprocal of the pseudopotential model's FP32 path.  Default: correctly rounded.
-// LBM_PP_FAST_RCP=1 selects the hardware approximation (rcp.approx) refined by one
-// Newton-Raphson step for 1/x, r <- r + r (1 - x r), in two FMAs: about 1% faster, but any
-// change of FP32 rounding moves the slow neutral modes of a static interface (e.g. a slab's
-// translation) by ~1e-5 over thousands of steps, at the edge of the parity bar.
-#ifndef LBM_PP_FAST_RCP
-#define LBM_PP_FAST_RCP 0
-#endif
-__device__ __forceinline__ float rcp_pp(float x) {
-#if LBM_PP_FAST_RCP
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    const float e = fmaf(-x, r, 1.0f);
-    return fmaf(r, e, r);
-#else
-    return __frcp_rn(x);
-#endif
-}
-__device__ __forceinline__ double rcp_pp(double x) { return 1.0 / x; }
 
 template <typename real>
 __device__ __forceinline__ real cs_pressure(real rho, real RT, real a, real b4) {
     const real e = b4 * rho;
-    const real r = rcp_pp(real(1) - e);
+    const real r = rcp(real(1) - e);
     const real num = real(1) + e * (real(1) + e * (real(1) - e));
     return rho * RT * num * (r * r * r) - a * rho * rho;
 }
@@ -178,7 +159,7 @@ __device__ __forceinline__ void pp_collide(real v[9], real rho, real pc, const r
     // Eq. (6b) and the moments m = M f (Eq. S48)
     const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
     const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
-    const real inv_rho = rcp_pp(rho);
+    const real inv_rho = rcp(rho);
     const real ux = (jx + real(0.5) * Fx) * inv_rho;
     const real uy = (jy + real(0.5) * Fy) * inv_rho;
     const real sax = (v[1] + v[2]) + (v[3] + v[4]);
@@ -384,6 +365,88 @@ __device__ __forceinline__ void fe_collide_v(F v[9], F rho, const F mn[9], const
     const F dpxx = fmav(F::c(2.0f * hn), fmav(ux, Gx, -(uy * Gy)), F::c(-P.s_nu) * (pxx - rho * fmav(ux, ux, -(uy * uy))));
     const F dpxy = fmav(F::c(hn), fmav(ux, Gy, uy * Gx), F::c(-P.s_nu) * (pxy - rho * ux * uy));
     apply_dm_v(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+}
+
+// Carnahan-Starling pressure (Eq. 28) and pseudopotential (Eq. 11, G = -1), explicit ops.
+template <class F>
+__device__ __forceinline__ F cs_pressure_v(F rho, const StepParams<float>& P) {
+    const F e = F::c(P.b4) * rho;
+    const F r = rcp_v(F::c(1.0f) - e);
+    const F num = fmav(e, fmav(e, F::c(1.0f) - e, F::c(1.0f)), F::c(1.0f));  // 1 + e (1 + e (1 - e))
+    return fmav(rho * F::c(P.RT) * num, r * r * r, -(F::c(P.a) * rho * rho));
+}
+__device__ __forceinline__ F1 sqrt_v(F1 x) { return F1(__fsqrt_rn(x.v)); }
+__device__ __forceinline__ F2 sqrt_v(F2 x) { return F2(__fsqrt_rn(x.v.x), __fsqrt_rn(x.v.y)); }
+template <class F>
+__device__ __forceinline__ F pseudo_psi_v(F rho, const StepParams<float>& P) {
+    return sqrt_v(F::c(2.0f) * fmav(rho, F::c(1.0f / 3.0f), -cs_pressure_v(rho, P)));
+}
+
+// Modified pseudopotential collision (Eqs. 1, 4, 6, 10, 13, 30-32) in the algebra of pp_collide:
+// pc = psi at the cell, pn[i] = psi at x + c_i (i = 1..8).
+template <class F>
+__device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9], const StepParams<float>& P) {
+    const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
+    const F Sx = fmav(pn[1] - pn[3], w1, ((pn[5] - pn[7]) + (pn[8] - pn[6])) * w2);
+    const F Sy = fmav(pn[2] - pn[4], w1, ((pn[5] - pn[7]) + (pn[6] - pn[8])) * w2);
+    const F Fx = fmav(pc, Sx, F::c(P.fx)), Fy = fmav(pc, Sy, F::c(P.fy));
+    const F d1 = pn[1] - pc, d2 = pn[2] - pc, d3 = pn[3] - pc, d4 = pn[4] - pc;
+    const F d5 = pn[5] - pc, d6 = pn[6] - pc, d7 = pn[7] - pc, d8 = pn[8] - pc;
+    const F dd = ((d5 + d6) + (d7 + d8)) * w2;
+    const F sxx = fmav(d1 + d3, w1, dd);
+    const F syy = fmav(d2 + d4, w1, dd);
+    const F sa = (sxx + syy) - dd;
+    const F sxy = ((d5 - d6) + (d7 - d8)) * w2;
+    const F Qxx = pc * fmav(F::c(P.kA), sa, F::c(P.kB) * sxx);
+    const F Qyy = pc * fmav(F::c(P.kA), sa, F::c(P.kB) * syy);
+    const F Qxy = pc * (F::c(P.kB) * sxy);
+    const F L = F::c(P.li) * fmav(Sx, Sx, Sy * Sy);
+    const F jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const F jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const F inv_rho = rcp_v(rho);
+    const F ux = fmav(F::c(0.5f), Fx, jx) * inv_rho;
+    const F uy = fmav(F::c(0.5f), Fy, jy) * inv_rho;
+    const F sax = (v[1] + v[2]) + (v[3] + v[4]);
+    const F sdg = (v[5] + v[6]) + (v[7] + v[8]);
+    const F e = fmav(F::c(-4.0f), v[0], fmav(F::c(2.0f), sdg, -sax));
+    const F z = fmav(F::c(4.0f), v[0], fmav(F::c(-2.0f), sax, sdg));
+    const F qx = fmav(F::c(2.0f), v[3] - v[1], (v[5] - v[6]) + (v[8] - v[7]));
+    const F qy = fmav(F::c(2.0f), v[4] - v[2], (v[5] + v[6]) - (v[7] + v[8]));
+    const F pxx = (v[1] + v[3]) - (v[2] + v[4]);
+    const F pxy = (v[5] + v[7]) - (v[6] + v[8]);
+    const F uu = fmav(ux, ux, uy * uy);
+    const F uF = fmav(ux, Fx, uy * Fy);
+    const F Ls = fmav(F::c(1.5f), Qxx + Qyy, L);  // L + 1.5 tr Q
+    const float he = 1.0f - 0.5f * P.s_e, hz = 1.0f - 0.5f * P.s_z, hq = 1.0f - 0.5f * P.s_q,
+                hn = 1.0f - 0.5f * P.s_nu;
+    // m* - m = -L (m - m^eq) + (I - L/2) MF' + MC  (Eqs. 1, 4/S66, 32, 13)
+    const F de = fmav(F::c(6.0f * he), uF, fmav(F::c(P.s_e), Ls, F::c(-P.s_e) * (e - rho * fmav(F::c(3.0f), uu, F::c(-2.0f)))));
+    const F dz = fmav(F::c(-6.0f * hz), uF, fmav(F::c(-P.s_z), Ls, F::c(-P.s_z) * (z - rho * fmav(F::c(-3.0f), uu, F::c(1.0f)))));
+    const F dqx = fmav(F::c(-hq), Fx, F::c(-P.s_q) * fmav(rho, ux, qx));
+    const F dqy = fmav(F::c(-hq), Fy, F::c(-P.s_q) * fmav(rho, uy, qy));
+    const F dpxx = fmav(F::c(2.0f * hn), fmav(ux, Fx, -(uy * Fy)),
+                        F::c(-P.s_nu) * ((pxx - rho * fmav(ux, ux, -(uy * uy))) + (Qxx - Qyy)));
+    const F dpxy = fmav(F::c(hn), fmav(ux, Fy, uy * Fx), F::c(-P.s_nu) * ((pxy - rho * ux * uy) + Qxy));
+    // j* - j = F exactly (tau_j drops out)
+    apply_dm_v(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+}
+
+// FP32 single-cell entry points used by every FP32 pseudopotential kernel (step, batch,
+// observables); the templates above serve FP64.
+__device__ __forceinline__ float pseudo_psi(float rho, const StepParams<float>& P) {
+    return pseudo_psi_v(F1(rho), P).v;
+}
+__device__ __forceinline__ void pp_collide(float v[9], float rho, float pc, const float pn[9],
+                                           const StepParams<float>& P) {
+    F1 vv[9], n[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        vv[i] = F1(v[i]);
+        n[i] = F1(pn[i]);
+    }
+    pp_collide_v(vv, F1(rho), F1(pc), n, P);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = vv[i].v;
 }
 
 // FP32 single-cell entry points used by every FP32 free-energy kernel (the templates above

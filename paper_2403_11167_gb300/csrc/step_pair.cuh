@@ -1,4 +1,5 @@
-// step_pair.cuh -- FP32 free-energy step: warp-independent windows, two cells per lane.
+// step_pair.cuh -- FP32 step kernels of both models: warp-independent windows, two cells
+// per lane.  (The free-energy kernel is described first; the pseudopotential kernel at the end.)
 //
 // Per-cell arithmetic: fe_mu_v / fe_collide_v (lbm_kernels.cuh) on F2, Blackwell's packed
 // FP32, so one instruction updates both cells of a lane; results are bitwise those of the
@@ -158,6 +159,92 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
         r1 = r0;
         m3 = m2;
         m2 = m1;
+    }
+    if (!ok) atomicExch(err, 1);
+}
+
+// Pseudopotential step (Eqs. 1, 4, 6, 10, 11, 13, 28, 30-32), two cells per lane.
+// Consumer warp iteration q: pull row q (staged rows q-1..q+1), psi(q); collide row q-1 with
+// psi rows q-2..q, re-pulling its populations from staged rows q-2..q; release the stage of
+// row q-2.  Lanes 0 and nw/2 + 1 supply the psi halo columns.
+template <int NW, int S>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) pp_step_pair(const float* __restrict__ fin,
+                                                                 float* __restrict__ fout, const StepParams<float> P,
+                                                                 int* __restrict__ err) {
+    constexpr int TXW = 60;
+    using Smem = WarpStripSmem<NW, S, TXW>;
+    constexpr int W8 = Smem::W8;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    const int nx = P.nx;
+    const int wb = warp_strip_width(nx, gridDim.x);
+    const int x0 = blockIdx.x * wb;
+    const int w = min(wb, nx - x0);
+    if (w <= 0) return;
+    const int y0 = blockIdx.y * P.rows;
+    const int y1 = min(y0 + P.rows, P.ny);
+    const int rbase = y0 - 2;
+    const int nsrc = y1 - y0 + 4;  // source rows y0-2 .. y1+1 (psi rows y0-1 .. y1)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NW);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == NW) {  // producer warp
+        if (lane == 0) {
+            int issued = 0;
+            if (!ring_produce<S, W8>(fin, P, rbase, nsrc, x0, w, sm.stage, sm.full, sm.empty, &issued)) {
+                atomicExch(err, 1);
+                drain_stages<S>(sm.full, issued);
+            }
+        }
+        return;
+    }
+    const int ww = (((w + NW - 1) / NW) + 1) & ~1;
+    const int cw = warp * ww;
+    const int nw = max(0, min(ww, w - cw));
+    const int col = cw - 2 + 2 * lane;
+    const bool act = nw > 0 && 2 * lane <= nw + 2;
+    const bool out = act && lane >= 1 && 2 * lane <= nw;
+    const int sc = col + 4;
+    Row2 p1, p2;  // psi of rows q-1, q-2
+    p1.c = p2.c = F2::c(0.0f);
+    p1.L = p1.R = p2.L = p2.R = 0.0f;
+    F2 rho1 = F2::c(1.0f);  // rho of row q-1
+    bool ok = mbar_wait_bounded(&sm.full[0], 0) && mbar_wait_bounded(&sm.full[1], 0);
+#pragma unroll 1
+    for (int q = y0 - 1; q <= y1 && ok; ++q) {
+        const int k = q + 1 - rbase;  // ring index of row q+1
+        ok = mbar_wait_bounded(&sm.full[k % S], (uint32_t)((k / S) & 1));
+        if (!ok) break;
+        F2 rho0 = F2::c(1.0f), psi = F2::c(0.0f);
+        if (act) {
+            F2 v[9];
+            pull_pair<W8>(sm.stage[(k - 2) % S], sm.stage[(k - 1) % S], sm.stage[k % S], sc, v);
+            rho0 = sum9_v(v);
+            psi = pseudo_psi_v(rho0, P);
+        }
+        const Row2 p0 = with_neighbours(psi);
+        // collide row q-1 (ring indices k-3 .. k-1 hold source rows q-2 .. q)
+        if (out && q > y0) {
+            F2 v[9], pn[9];
+            pull_pair<W8>(sm.stage[(k - 3) % S], sm.stage[(k - 2) % S], sm.stage[(k - 1) % S], sc, v);
+            neighbours_pair(p2, p1, p0, pn);
+            pp_collide_v(v, rho1, pn[0], pn, P);
+            float* o = fout + (long long)(q - 1) * nx + x0 + col;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) *reinterpret_cast<float2*>(o + i * P.pitch) = v[i].v;
+        }
+        // row q-2 (ring index k-3) is no longer read by this warp
+        __syncwarp();
+        if (lane == 0 && k >= 3) mbar_arrive(&sm.empty[(k - 3) % S]);
+        p2 = p1;
+        p1 = p0;
+        rho1 = rho0;
     }
     if (!ok) atomicExch(err, 1);
 }
