@@ -33,6 +33,7 @@
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
 #include "step_tma.cuh"
+#include "step_pair.cuh"
 
 namespace {
 
@@ -47,8 +48,18 @@ int bfail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return bfail(e_, #call);       \
     } while (0)
 
-constexpr int kBTX = 256;        // strip width of the tiled batch kernel
+constexpr int kBTX = 256;        // strip width of the one-cell tiled batch kernel
 constexpr int kBS = 6;           // its stage count
+// Tiled lattices run the two-cells-per-lane strip of the context path (1) or the one-cell
+// CTA-synchronised strip (0).
+#ifndef LBM_BATCH_PAIR
+#define LBM_BATCH_PAIR 1
+#endif
+constexpr bool kBPair = LBM_BATCH_PAIR != 0;
+constexpr int kBPWarps = 4;
+constexpr int kBPStages = 6;
+using BPSmem = lbmk::WarpStripSmem<kBPWarps, kBPStages, 60>;
+constexpr int kBPTX = BPSmem::TX;  // widest pair strip (240 columns)
 constexpr int kChunk = 64;       // steps per captured graph
 constexpr size_t kResidentSmemMax = 200 * 1024;
 
@@ -144,6 +155,22 @@ __global__ void __launch_bounds__(TX + 32, LBM_PP_MINB)
     if (step >= L.nsteps) return;
     const StepParams<float> P = L.P;
     pp_strip_tma<TX, S>(L.buf[step & 1], L.buf[(step + 1) & 1], P, it.x0, it.w, it.y0, it.y1, sm, err);
+}
+
+// Tiled lattices, two cells per lane: one strip of one lattice per CTA, one step per launch.
+template <int NW, int S>
+__global__ void __launch_bounds__((NW + 1) * 32, 1)
+    pp_batch_pair(const BatchLattice* __restrict__ lats, const BatchItem* __restrict__ items,
+                  const int* __restrict__ step_base, int k, int* __restrict__ err) {
+    using Smem = WarpStripSmem<NW, S, 60>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    const BatchItem it = items[blockIdx.x];
+    const BatchLattice& L = lats[it.lat];
+    const int step = *step_base + k;
+    if (step >= L.nsteps) return;
+    const StepParams<float> P = L.P;
+    pp_pair_strip<NW, S>(L.buf[step & 1], L.buf[(step + 1) & 1], P, it.x0, it.w, it.y0, it.y1, sm, err);
 }
 
 __global__ void advance_step(int* step_base, int by) { *step_base += by; }
@@ -312,8 +339,12 @@ int launch_resident(lbm_batch* b, int step_limit, cudaStream_t s) {
 
 int launch_tiled_step(lbm_batch* b, int k, cudaStream_t s) {
     if (b->items.empty()) return LBM_OK;
-    lbmk::pp_batch_tma<kBTX, kBS><<<(unsigned)b->items.size(), kBTX + 32, sizeof(lbmk::PPTmaSmem<kBTX, kBS>), s>>>(
-        b->d_lat, b->d_items, b->d_step, k, b->d_err);
+    if (kBPair)
+        lbmk::pp_batch_pair<kBPWarps, kBPStages><<<(unsigned)b->items.size(), (kBPWarps + 1) * 32, sizeof(BPSmem), s>>>(
+            b->d_lat, b->d_items, b->d_step, k, b->d_err);
+    else
+        lbmk::pp_batch_tma<kBTX, kBS><<<(unsigned)b->items.size(), kBTX + 32, sizeof(lbmk::PPTmaSmem<kBTX, kBS>), s>>>(
+            b->d_lat, b->d_items, b->d_step, k, b->d_err);
     BCK(cudaGetLastError());
     return LBM_OK;
 }
@@ -329,9 +360,12 @@ void build_items(lbm_batch* b, int rows) {
         const int nx = b->lat[i].P.nx, ny = b->lat[i].P.ny;
         const int r = std::min(rows, ny);
         b->lat[i].P.rows = r;
+        // pair strips: nx split into equal widths (multiples of 4, at most kBPTX columns)
+        const int gx = (nx + kBPTX - 1) / kBPTX;
+        const int wb = kBPair ? lbmk::warp_strip_width(nx, gx) : kBTX;
         for (int y0 = 0; y0 < ny; y0 += r)
-            for (int x0 = 0; x0 < nx; x0 += kBTX)
-                b->items.push_back(BatchItem{i, x0, std::min(kBTX, nx - x0), y0, std::min(y0 + r, ny)});
+            for (int x0 = 0; x0 < nx; x0 += wb)
+                b->items.push_back(BatchItem{i, x0, std::min(wb, nx - x0), y0, std::min(y0 + r, ny)});
     }
 }
 
@@ -593,8 +627,10 @@ extern "C" int lbm_batch_create(int n, const lbm_batch_lattice* specs, const dou
             return fail(bfail(e, "cudaFuncSetAttribute(resident smem)"));
     }
     if ((e = cudaFuncSetAttribute(lbmk::pp_batch_tma<kBTX, kBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sizeof(lbmk::PPTmaSmem<kBTX, kBS>))) != cudaSuccess)
-        return fail(bfail(e, "cudaFuncSetAttribute(batch tma smem)"));
+                                  (int)sizeof(lbmk::PPTmaSmem<kBTX, kBS>))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(lbmk::pp_batch_pair<kBPWarps, kBPStages>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BPSmem))) != cudaSuccess)
+        return fail(bfail(e, "cudaFuncSetAttribute(batch strip smem)"));
     build_items(b, 32);
     if ((rc = upload_tables(b))) return fail(rc);
     if ((rc = batch_init_state(b))) return fail(rc);

@@ -167,22 +167,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
 // Consumer warp iteration q: pull row q (staged rows q-1..q+1), psi(q); collide row q-1 with
 // psi rows q-2..q, re-pulling its populations from staged rows q-2..q; release the stage of
 // row q-2.  Lanes 0 and nw/2 + 1 supply the psi halo columns.
+// One CTA's strip of the pseudopotential step: columns [x0, x0 + w) (w <= 60 NW, x0 and w
+// multiples of 4), rows [y0, y1).  Called by every thread of the CTA.
 template <int NW, int S>
-__global__ void __launch_bounds__((NW + 1) * 32, 1) pp_step_pair(const float* __restrict__ fin,
-                                                                 float* __restrict__ fout, const StepParams<float> P,
-                                                                 int* __restrict__ err) {
-    constexpr int TXW = 60;
-    using Smem = WarpStripSmem<NW, S, TXW>;
-    constexpr int W8 = Smem::W8;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+__device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, float* __restrict__ fout,
+                                              const StepParams<float>& P, int x0, int w, int y0, int y1,
+                                              WarpStripSmem<NW, S, 60>& sm, int* __restrict__ err) {
+    constexpr int W8 = WarpStripSmem<NW, S, 60>::W8;
     const int nx = P.nx;
-    const int wb = warp_strip_width(nx, gridDim.x);
-    const int x0 = blockIdx.x * wb;
-    const int w = min(wb, nx - x0);
-    if (w <= 0) return;
-    const int y0 = blockIdx.y * P.rows;
-    const int y1 = min(y0 + P.rows, P.ny);
     const int rbase = y0 - 2;
     const int nsrc = y1 - y0 + 4;  // source rows y0-2 .. y1+1 (psi rows y0-1 .. y1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -247,6 +239,21 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) pp_step_pair(const float* __
         rho1 = rho0;
     }
     if (!ok) atomicExch(err, 1);
+}
+
+template <int NW, int S>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) pp_step_pair(const float* __restrict__ fin,
+                                                                 float* __restrict__ fout, const StepParams<float> P,
+                                                                 int* __restrict__ err) {
+    using Smem = WarpStripSmem<NW, S, 60>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    const int wb = warp_strip_width(P.nx, gridDim.x);
+    const int x0 = blockIdx.x * wb;
+    const int w = min(wb, P.nx - x0);
+    if (w <= 0) return;
+    const int y0 = blockIdx.y * P.rows;
+    pp_pair_strip<NW, S>(fin, fout, P, x0, w, y0, min(y0 + P.rows, P.ny), sm, err);
 }
 
 }  // namespace lbmk
