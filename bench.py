@@ -58,6 +58,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device="cpu") -> float:
+    """The largest of every rank's x (the job takes as long as its slowest rank); x itself when
+    the job has one rank.  Collective over the default process group (NCCL on GPUs, gloo in
+    the CPU tests)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / seconds
+
+
 def workload_config(args):
     return {
         "workload": f"spinodal decomposition, {args.size}x{args.size} periodic D2Q9, Carnahan-Starling a=0.25 "
@@ -400,12 +419,10 @@ def run_ours(args):
         elapsed_ms = t0.elapsed_time(t1)
         per_model_ms = [sum(kev[k][m][0].elapsed_time(kev[k][m][1]) for k in range(args.steps)) for m in range(2)]
 
-    elapsed = torch.tensor([elapsed_ms], device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(elapsed, op=torch.distributed.ReduceOp.MAX)
-    elapsed_ms = float(elapsed.item())
-    updates = ws * args.steps * 2 * nsteps * ncell
-    value = updates / (elapsed_ms * 1e-3) / 1e6
+    elapsed_ms = max_over_ranks(elapsed_ms, ws, device="cuda")
+    updates_per_rank = args.steps * 2 * nsteps * ncell
+    updates = ws * updates_per_rank
+    value = job_rate(updates_per_rank, ws, elapsed_ms * 1e-3) / 1e6
 
     # end to end through the public API: pinned host rho0 -> H2D -> steps -> observables D2H
     e2e = None
@@ -418,12 +435,8 @@ def run_ours(args):
                 ctx.step(nsteps)
                 ctx.observables(0)
         barrier()
-        e2e_s = time.perf_counter() - t
-        t_all = torch.tensor([e2e_s], device="cuda")
-        if ws > 1:
-            torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t_all.item())
-        e2e = {"value": updates / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 2 * ncell * 8,
+        e2e_s = max_over_ranks(time.perf_counter() - t, ws, device="cuda")
+        e2e = {"value": job_rate(updates_per_rank, ws, e2e_s) / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 2 * ncell * 8,
                "d2h_bytes_per_step": 2 * 8 * 8}
 
     if rank != 0:

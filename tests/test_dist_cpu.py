@@ -1,0 +1,63 @@
+"""The multi-rank (replica) host logic of the benchmark, run as two gloo ranks on the CPU:
+the job's time is the slowest rank's, and the job's throughput counts every rank's units.
+Each rank processes its own independent lattices, so there is no data-path collective to
+test; only the timing reduction crosses ranks."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, q):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        env = bench.dist_env()
+        local_ms = [120.0, 95.5][rank]
+        slowest = bench.max_over_ranks(local_ms, ws)
+        dist.barrier()
+        rate = bench.job_rate(1000.0, ws, slowest * 1e-3)
+        q.put((rank, env, slowest, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time_and_sum_the_work():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, env, slowest, rate in out:
+        assert env == (2, rank, rank)
+        assert slowest == 120.0
+        assert rate == pytest.approx(2 * 1000.0 / 0.120)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+    assert bench.job_rate(10.0, 1, 2.0) == 5.0
