@@ -343,6 +343,15 @@ void* lbm_stream(const lbm_ctx* ctx);
 void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_strerror(int status);
 
+/* Self-test of the bounded device waits that guard the TMA pipelines (the paper has no
+ * counterpart; failure detection of this library).  Launches one 64-thread block that
+ * waits on a shared-memory mbarrier phase for at most `polls` polls (1 .. 2^22): with
+ * arrive = 0 nothing completes the phase, the wait gives up and the call returns
+ * LBM_ERR_TIMEOUT while the device context stays usable; with arrive = 1 the phase is
+ * completed first and the call returns LBM_OK.  Synchronises the device.  LBM_ERR_ARG for
+ * other arguments, LBM_ERR_CUDA on a CUDA failure. */
+int lbm_selftest_bounded_wait(int arrive, int polls);
+
 /* Library build information: "sm_103a ..." string. */
 const char* lbm_build_info(void);
 

@@ -131,6 +131,42 @@ extern "C" const char* lbm_strerror(int s) {
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Self-test of the bounded device wait (failure detection without a fault): one CTA
+// initialises an mbarrier and waits, with a short poll limit, for its first phase.  With
+// arrive = 0 nothing ever completes that phase, so every thread gives up, records the
+// timeout and the CTA exits normally; with arrive = 1 thread 0 completes the phase first.
+namespace {
+__device__ int g_selftest_flag;
+
+__global__ void bounded_wait_selftest_kernel(int arrive, uint32_t polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        lbmk::mbar_init(&bar, 1);
+        lbmk::fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0)
+        asm volatile(
+            "{\n\t.reg .b64 st;\n\t"
+            "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(lbmk::smem_u32(&bar))
+            : "memory");
+    if (!lbmk::mbar_wait_polls(&bar, 0, polls)) atomicExch(&g_selftest_flag, 1);
+}
+}  // namespace
+
+extern "C" int lbm_selftest_bounded_wait(int arrive, int polls) {
+    if (polls < 1 || polls > (1 << 22) || (arrive != 0 && arrive != 1)) return LBM_ERR_ARG;
+    const int zero = 0;
+    CK(cudaMemcpyToSymbol(g_selftest_flag, &zero, sizeof(int)));
+    bounded_wait_selftest_kernel<<<1, 64>>>(arrive, (uint32_t)polls);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    int flag = 0;
+    CK(cudaMemcpyFromSymbol(&flag, g_selftest_flag, sizeof(int)));
+    return flag ? LBM_ERR_TIMEOUT : LBM_OK;
+}
+
 extern "C" const char* lbm_build_info(void) {
     return "gb300 D2Q9 multiphase LBM; sm_103a; fused pull collide+stream; "
            "pseudopotential (MP-LBM) and improved well-balanced free energy";

@@ -53,13 +53,19 @@ __device__ __forceinline__ bool mbar_test_parity(uint64_t* bar, uint32_t parity)
     return done != 0;
 }
 
-// Bounded wait for a phase of an mbarrier; false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
+// Wait for a phase of an mbarrier for at most max_polls polls (with backoff after 64);
+// false on timeout.
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, uint32_t max_polls) {
+    for (uint32_t it = 0; it < max_polls; ++it) {
         if (mbar_test_parity(bar, parity)) return true;
         if (it > 64) __nanosleep(64);
     }
     return false;
+}
+
+// Bounded wait of the step kernels (2^22 polls, well under a second); false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    return mbar_wait_polls(bar, parity, 1u << 22);
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

@@ -136,6 +136,7 @@ def _lib():
             "lbm_batch_stream": ([vp], vp),
             "lbm_batch_destroy": ([vp], None),
             "lbm_batch_last_error": ([], ctypes.c_char_p),
+            "lbm_selftest_bounded_wait": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "lbm_resolve_params_many": ([ctypes.c_int, P, P, T, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "lbm_surrogate_num_params": ([], ctypes.c_int),
             "lbm_surrogate_create": ([fp, ctypes.c_uint, ctypes.POINTER(vp)], ctypes.c_int),
@@ -500,3 +501,8 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def lbm_selftest_bounded_wait(arrive: bool, polls: int) -> int:
+    """Status of one bounded device wait (LBM_OK or LBM_ERR_TIMEOUT); see include/lbm.h."""
+    return _lib().lbm_selftest_bounded_wait(1 if arrive else 0, polls)
