@@ -4,8 +4,8 @@
 // Per-cell arithmetic: fe_mu_v / fe_collide_v (lbm_kernels.cuh) on F2, Blackwell's packed
 // FP32, so one instruction updates both cells of a lane; results are bitwise those of the
 // single-cell kernels.  Data movement: the TMA row ring of step_warp.cuh (one producer warp,
-// per-stage full/empty mbarriers, no CTA barrier per row).  Each consumer warp owns at most
-// 60 columns plus two halo columns on each side, two adjacent columns per lane: it keeps rho
+// per-stage full/empty mbarriers, no CTA barrier per row).  Each consumer warp owns a run of
+// 60 columns (the last one fewer; warps beyond the strip stay idle) plus two halo columns on each side, two adjacent columns per lane: it keeps rho
 // of the last four rows and mu of the last three in registers, reads x-neighbours with warp
 // shuffles, and re-pulls the populations of the row it collides (two rows behind the row it
 // pulls) from the ring, which therefore holds rows q-3 .. q+1 of every warp plus prefetch.
@@ -87,10 +87,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
     const int rbase = y0 - 3;
     const int nsrc = y1 - y0 + 6;  // source rows y0-3 .. y1+2 (rho rows y0-2 .. y1+1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // consumer warps fill 60-column runs from the left; only the warps with columns run (a
+    // narrow strip leaves the others idle instead of spreading few lanes over all of them)
+    const int nwa = min(NW, (w + 59) / 60);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], NW);
+            mbar_init(&sm.empty[s], nwa);
         }
         fence_mbar_init();
     }
@@ -105,11 +108,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
         }
         return;
     }
-    // consumer warp: columns [cw, cw + nw) of the strip (nw even), lane l at columns
+    if (warp >= nwa) return;
+    // consumer warp: columns [cw, cw + nw) of the strip (nw even, > 0), lane l at columns
     // cw - 2 + 2l and cw - 1 + 2l
-    const int ww = (((w + NW - 1) / NW) + 1) & ~1;
-    const int cw = warp * ww;
-    const int nw = max(0, min(ww, w - cw));
+    const int cw = warp * 60;
+    const int nw = min(60, w - cw);
     const int col = cw - 2 + 2 * lane;
     const bool act = nw > 0 && 2 * lane <= nw + 2;           // rho and mu lanes
     const bool out = act && lane >= 1 && 2 * lane <= nw;     // both cells inside the warp's run
@@ -178,10 +181,13 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
     const int rbase = y0 - 2;
     const int nsrc = y1 - y0 + 4;  // source rows y0-2 .. y1+1 (psi rows y0-1 .. y1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // consumer warps fill 60-column runs from the left; only the warps with columns run (a
+    // narrow strip leaves the others idle instead of spreading few lanes over all of them)
+    const int nwa = min(NW, (w + 59) / 60);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], NW);
+            mbar_init(&sm.empty[s], nwa);
         }
         fence_mbar_init();
     }
@@ -196,9 +202,9 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
         }
         return;
     }
-    const int ww = (((w + NW - 1) / NW) + 1) & ~1;
-    const int cw = warp * ww;
-    const int nw = max(0, min(ww, w - cw));
+    if (warp >= nwa) return;
+    const int cw = warp * 60;
+    const int nw = min(60, w - cw);
     const int col = cw - 2 + 2 * lane;
     const bool act = nw > 0 && 2 * lane <= nw + 2;
     const bool out = act && lane >= 1 && 2 * lane <= nw;
