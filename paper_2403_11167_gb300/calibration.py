@@ -222,3 +222,45 @@ def fit_surrogate(X, Y, seed=0, weights=LOSS_WEIGHTS, **train_cfg):
     t0 = time.perf_counter()
     loss = m.train(X, Y, **cfg)
     return m, loss, time.perf_counter() - t0
+
+
+class SurrogateCalibration:
+    """Calibration with the trained surrogate and the plain calibration runs as its fallback.
+
+    The surrogate answers a parameter set only inside the domain it was trained on: Tr, a
+    and b within the ranges of the valid training sets, kappa_P one of the trained values.
+    Its sigma is used only for kappa_P values where at least ``min_sigma_fraction`` of the
+    valid training sets had a measurable sigma (thin interfaces, kappa_P = 0.4, mostly have
+    none).  Every other set is calibrated by running its lattices (``calibrate_batched``,
+    bitwise the plain one-lattice-at-a-time calibration), and its whole row comes from that
+    run.
+    """
+
+    def __init__(self, surrogate, X_train, Y_train, ok_train, min_sigma_fraction=0.5):
+        X = np.asarray(X_train, dtype=np.float64)[ok_train]
+        Y = np.asarray(Y_train, dtype=np.float64)[ok_train]
+        self.m = surrogate
+        self.lo = X[:, :3].min(axis=0)
+        self.hi = X[:, :3].max(axis=0)
+        self.kappas = np.unique(X[:, 3])
+        self.sigma_ok = {float(k): float(np.isfinite(Y[X[:, 3] == k, 3]).mean()) >= min_sigma_fraction
+                         for k in self.kappas}
+
+    def inside(self, X):
+        X = np.asarray(X, dtype=np.float64)
+        in_box = np.all((X[:, :3] >= self.lo) & (X[:, :3] <= self.hi), axis=1)
+        known = np.isin(X[:, 3], self.kappas)
+        with_sigma = np.array([self.sigma_ok.get(float(k), False) for k in X[:, 3]])
+        return in_box & known & with_sigma
+
+    def calibrate(self, sets):
+        """(Y n x 4, source: 'surrogate' or 'calibration' per set)."""
+        X = features(sets)
+        use = self.inside(X)
+        Y = np.full((len(sets), 4), np.nan)
+        if use.any():
+            Y[use] = self.m.predict(X[use])
+        rest = [s for s, u in zip(sets, use) if not u]
+        if rest:
+            Y[~use] = calibrate_batched(rest)["Y"]
+        return Y, np.where(use, "surrogate", "calibration")

@@ -253,3 +253,21 @@ def test_surrogate_gain_over_theory(calibrated):
     for j in (2, 3):
         m_ = sig if j == 3 else ok
         assert np.mean(np.abs(P[m_, j] / rh["Y"][m_, j] - 1)) < np.mean(np.abs(T[m_, j] / rh["Y"][m_, j] - 1))
+
+
+def test_plain_calibration_is_the_fallback_outside_the_trained_domain(calibrated):
+    """Sets inside the trained domain get the network's answer; a set beyond the trained
+    temperatures, one with an untrained width parameter and one with kappa_P = 0.4 (whose
+    training sets mostly lack a measurable sigma) are calibrated by running their lattices,
+    exactly as a plain calibration does."""
+    C, r, m, tr = calibrated["C"], calibrated["r"], calibrated["m"], calibrated["tr"]
+    sc = C.SurrogateCalibration(m, C.features(tr), r["Y"], r["ok"])
+    assert not sc.sigma_ok[0.4] and sc.sigma_ok[0.7] and sc.sigma_ok[1.0]
+    inside = [dict(Tr=0.6, a=0.3, b=3.5, kappa_P=0.7), dict(Tr=0.7, a=0.45, b=4.5, kappa_P=1.0),
+              dict(Tr=0.8, a=0.26, b=4.0, kappa_P=0.7), dict(Tr=0.9, a=0.4, b=3.2, kappa_P=1.0)]
+    outside = [dict(Tr=0.97, a=0.3, b=4.0, kappa_P=1.0), dict(Tr=0.7, a=0.3, b=4.0, kappa_P=0.85),
+               dict(Tr=0.7, a=0.3, b=4.0, kappa_P=0.4)]
+    Y, src = sc.calibrate(inside + outside)
+    assert list(src) == ["surrogate"] * 4 + ["calibration"] * 3
+    assert np.array_equal(Y[:4], m.predict(C.features(inside)))
+    assert np.array_equal(Y[4:], C.calibrate_batched(outside)["Y"], equal_nan=True)
