@@ -10,7 +10,8 @@
 //                         memory: one CTA per lattice runs every step of that lattice in
 //                         shared memory, in one persistent launch (no HBM traffic per step);
 //   tiled lattices     -- the rest: a work table of (lattice, strip) items; one launch per
-//                         time step runs the TMA strip kernel over every active lattice,
+//                         time step runs the two-cells-per-lane TMA strip of the context
+//                         path (pp_pair_strip) over every active lattice,
 //                         replayed as captured 64-step CUDA graphs on a second stream,
 //                         concurrently with the resident launch.
 //
@@ -572,7 +573,7 @@ extern "C" int lbm_batch_create(int n, const lbm_batch_lattice* specs, const dou
         L.resident = smem <= kResidentSmemMax;
         if (!L.resident && (s.nx % 4 != 0 || s.nx < 8 || s.ny < 4)) {
             delete b;
-            return LBM_ERR_UNSUPPORTED;  // tiled lattices use the TMA strip kernel
+            return LBM_ERR_UNSUPPORTED;  // tiled lattices use the TMA strip kernels
         }
         if (!L.resident) b->max_tiled_steps = std::max(b->max_tiled_steps, L.nsteps);
         offs[i] = pool_bytes;
