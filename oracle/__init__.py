@@ -48,6 +48,7 @@ class Params(ctypes.Structure):
         ("kappa_P", ctypes.c_double), ("kappa_Li", ctypes.c_double),
         ("sigma_Li", ctypes.c_double), ("kappa", ctypes.c_double),
         ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+        ("walls", ctypes.c_double),
     ]
 
 
@@ -55,7 +56,7 @@ def make_params(**kw) -> Params:
     """Build oracle parameters; unspecified relaxation times default to 1, G to -1."""
     d = dict(a=0.5, b=4.0, R=1.0, T=0.0, G=-1.0, tau_rho=1.0, tau_e=1.0, tau_zeta=1.0,
              tau_j=1.0, tau_q=1.0, tau_nu=1.0, kappa_P=1.0, kappa_Li=0.0, sigma_Li=0.0,
-             kappa=0.5, fx=0.0, fy=0.0)
+             kappa=0.5, fx=0.0, fy=0.0, walls=0.0)
     unknown = set(kw) - set(d)
     if unknown:
         raise KeyError(f"unknown oracle parameter(s): {sorted(unknown)}")

@@ -31,7 +31,8 @@
  *
  * Everything is done cell by cell with explicit 9x9 matrix products; no fusion,
  * no reordering beyond the equations.  Fields are SoA: f[i*ny*nx + y*nx + x],
- * periodic in both directions.
+ * periodic in x, and in y either periodic or bounded by no-slip walls on rows 0 and ny-1
+ * (the parallel-plate flow of Sec. 5.3, Zou and He's condition; see wall_fill).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -65,6 +66,7 @@ typedef struct {
     double kappa_P, kappa_Li, sigma_Li; /* MP-LBM, Eqs. (30)-(32) */
     double kappa;       /* FE-LBM surface-tension parameter, mu = mu_b - kappa lap rho */
     double fx, fy;      /* constant body force added to the total force */
+    double walls;       /* 0: periodic in y; 1: no-slip walls on rows 0 and ny-1 (Sec. 5.3) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -148,6 +150,16 @@ static inline int wrap(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
+/* Row of a y neighbour: periodic, or, with walls, mirrored through the wall node (the
+ * reading of this oracle: row -1 is row 1 and row ny is row ny-2, i.e. zero normal
+ * gradient of psi, rho and mu at a wall node; the paper does not specify it). */
+static inline int yrow(int y, int ny, int walls) {
+    if (!walls) return wrap(y, ny);
+    if (y < 0) return -y;
+    if (y > ny - 1) return 2 * (ny - 1) - y;
+    return y;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Equilibria.                                                               */
 /* Eq. (4): standard second-order equilibrium (used by the pseudopotential model). */
@@ -195,7 +207,7 @@ static void sc_force(const orc_params* p, const double* psi, int nx, int ny, int
                      double* Fx, double* Fy) {
     double sx = 0.0, sy = 0.0;
     for (int i = 1; i < Q9; ++i) {
-        double pn = psi[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)];
+        double pn = psi[yrow(y + CY[i], ny, p->walls != 0.0) * nx + wrap(x + CX[i], nx)];
         sx += omega_of(i) * pn * CX[i];
         sy += omega_of(i) * pn * CY[i];
     }
@@ -213,7 +225,7 @@ static void q_tensor(const orc_params* p, const double* psi, int nx, int ny, int
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) Q[a][b] = 0.0;
     for (int i = 1; i < Q9; ++i) {
-        double pn = psi[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)];
+        double pn = psi[yrow(y + CY[i], ny, p->walls != 0.0) * nx + wrap(x + CX[i], nx)];
         double c[2] = {(double)CX[i], (double)CY[i]};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
@@ -241,12 +253,52 @@ static void lambda_diag(const orc_params* p, double L[Q9]) {
     L[8] = 1.0 / p->tau_nu;
 }
 
+/* ------------------------------------------------------------------------ */
+/* No-slip walls on rows 0 and ny-1 (Sec. 5.3: Zou and He's velocity condition).  After
+ * streaming, a wall node lacks the populations that would come from beyond the wall
+ * (bottom: i = 2, 5, 6; top: i = 4, 7, 8).  They are set so that the node's momentum is
+ * J = rho u - F/2 with u = 0, i.e. J = -F/2 (Eq. 6b), Zou-He style:
+ *   bottom  f2 = f4 + 2/3 Jy,  f5 = f7 - (f1 - f3)/2 + Jx/2 + Jy/6,  f6 = f8 + (f1 - f3)/2 - Jx/2 + Jy/6
+ *   top     f4 = f2 - 2/3 Jy,  f7 = f5 + (f1 - f3)/2 - Jx/2 - Jy/6,  f8 = f6 - (f1 - f3)/2 + Jx/2 - Jy/6
+ * The node's density sum_i f_i then depends on Jy only, and the wall-normal force is the
+ * body force alone (the mirrored neighbours cancel the interaction part), so a first fill
+ * with Jy = -fy/2 and Jx = 0 fixes rho exactly; once the forces are known the fill is
+ * repeated with Jx = -Fx/2. */
+static void wall_fill(const orc_params* p, int nx, int ny, double* f, const double* Fx) {
+    size_t N = (size_t)nx * ny;
+    const double Jy = -p->fy / 2.0;
+    for (int side = 0; side < 2; ++side) {
+        const int y = side == 0 ? 0 : ny - 1;
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
+            double* g[Q9];
+            for (int i = 0; i < Q9; ++i) g[i] = &f[(size_t)i * N + c];
+            const double Jx = Fx ? -Fx[c] / 2.0 : 0.0;
+            const double d13 = *g[1] - *g[3];
+            if (side == 0) {
+                *g[2] = *g[4] + 2.0 / 3.0 * Jy;
+                *g[5] = *g[7] - d13 / 2.0 + Jx / 2.0 + Jy / 6.0;
+                *g[6] = *g[8] + d13 / 2.0 - Jx / 2.0 + Jy / 6.0;
+            } else {
+                *g[4] = *g[2] - 2.0 / 3.0 * Jy;
+                *g[7] = *g[5] + d13 / 2.0 - Jx / 2.0 - Jy / 6.0;
+                *g[8] = *g[6] - d13 / 2.0 + Jx / 2.0 - Jy / 6.0;
+            }
+        }
+    }
+}
+
+static inline int is_wall_row(const orc_params* p, int y, int ny) {
+    return p->walls != 0.0 && (y == 0 || y == ny - 1);
+}
+
 /* Density, psi, force and velocity of the pseudopotential model for the whole
  * lattice (Eqs. 6a, 11, 10, 6b). psi < 0 marks a negative radicand. */
-static int pp_fields(const orc_params* p, int nx, int ny, const double* f, double* rho,
+static int pp_fields(const orc_params* p, int nx, int ny, double* f, double* rho,
                      double* psi, double* Fx, double* Fy, double* ux, double* uy) {
     size_t N = (size_t)nx * ny;
     int bad = 0;
+    if (p->walls != 0.0) wall_fill(p, nx, ny, f, NULL);
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (long c = 0; c < (long)N; ++c) {
         double s = 0.0;
@@ -263,7 +315,13 @@ static int pp_fields(const orc_params* p, int nx, int ny, const double* f, doubl
             double fix, fiy;
             sc_force(p, psi, nx, ny, x, y, &fix, &fiy);
             Fx[c] = fix + p->fx;
-            Fy[c] = fiy + p->fy;
+            Fy[c] = is_wall_row(p, y, ny) ? p->fy : fiy + p->fy;
+        }
+    if (p->walls != 0.0) wall_fill(p, nx, ny, f, Fx);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
             double jx = 0.0, jy = 0.0;
             for (int i = 0; i < Q9; ++i) {
                 jx += f[(size_t)i * N + c] * CX[i];
@@ -278,7 +336,7 @@ static int pp_fields(const orc_params* p, int nx, int ny, const double* f, doubl
 /* One MP-LBM time step: collision per Eq. (1) with Eqs. (4), (13), (30)-(32), then
  * streaming f_i(x + c_i) <- f*_i(x).  f is read, fnew written.  Returns 0 or -1
  * if rho <= 0 or the psi radicand is negative somewhere. */
-static int pp_step(const orc_params* p, int nx, int ny, const double* f, double* fnew,
+static int pp_step(const orc_params* p, int nx, int ny, double* f, double* fnew,
                    double* rho, double* psi, double* Fx, double* Fy, double* ux, double* uy) {
     size_t N = (size_t)nx * ny;
     if (pp_fields(p, nx, ny, f, rho, psi, Fx, Fy, ux, uy)) return -1;
@@ -330,6 +388,7 @@ static int pp_step(const orc_params* p, int nx, int ny, const double* f, double*
                 double s = 0.0;
                 for (int k = 0; k < Q9; ++k) s += MINV[i][k] * dm[k];
                 int xd = wrap(x + CX[i], nx), yd = wrap(y + CY[i], ny);
+                if (p->walls != 0.0 && (y + CY[i] < 0 || y + CY[i] > ny - 1)) continue;  /* leaves through a wall */
                 fnew[(size_t)i * N + (size_t)yd * nx + xd] = fc[i] + s;
             }
         }
@@ -341,28 +400,29 @@ static int pp_step(const orc_params* p, int nx, int ny, const double* f, double*
 
 /* Eq. (24): grad phi = (1/c_s^2) sum_i w_i phi(x + c_i) c_i;
  *           lap phi  = (2/c_s^2) sum_i w_i [phi(x + c_i) - phi(x)]. */
-static void stencil_grad(const double* phi, int nx, int ny, int x, int y, double* gx, double* gy) {
+static void stencil_grad(const double* phi, int nx, int ny, int walls, int x, int y, double* gx, double* gy) {
     double sx = 0.0, sy = 0.0;
     for (int i = 0; i < Q9; ++i) {
-        double v = phi[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)];
+        double v = phi[yrow(y + CY[i], ny, walls) * nx + wrap(x + CX[i], nx)];
         sx += WI[i] * v * CX[i];
         sy += WI[i] * v * CY[i];
     }
     *gx = sx / CS2;
     *gy = sy / CS2;
 }
-static double stencil_lap(const double* phi, int nx, int ny, int x, int y) {
+static double stencil_lap(const double* phi, int nx, int ny, int walls, int x, int y) {
     double s = 0.0, pc = phi[y * nx + x];
-    for (int i = 0; i < Q9; ++i) s += WI[i] * (phi[wrap(y + CY[i], ny) * nx + wrap(x + CX[i], nx)] - pc);
+    for (int i = 0; i < Q9; ++i) s += WI[i] * (phi[yrow(y + CY[i], ny, walls) * nx + wrap(x + CX[i], nx)] - pc);
     return 2.0 / CS2 * s;
 }
 
 /* Density, chemical potential, gradients, force and velocity of the FE model. */
-static int fe_fields(const orc_params* p, int nx, int ny, const double* f, double* rho,
+static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho,
                      double* mu, double* Fx, double* Fy, double* ux, double* uy, double* drx,
                      double* dry) {
     size_t N = (size_t)nx * ny;
     int bad = 0;
+    if (p->walls != 0.0) wall_fill(p, nx, ny, f, NULL);
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (long c = 0; c < (long)N; ++c) {
         double s = 0.0;
@@ -375,17 +435,27 @@ static int fe_fields(const orc_params* p, int nx, int ny, const double* f, doubl
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;
-            mu[c] = mu_bulk(p, rho[c]) - p->kappa * stencil_lap(rho, nx, ny, x, y);
+            mu[c] = mu_bulk(p, rho[c]) - p->kappa * stencil_lap(rho, nx, ny, p->walls != 0.0, x, y);
         }
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;
             double gmx, gmy;
-            stencil_grad(mu, nx, ny, x, y, &gmx, &gmy);
-            stencil_grad(rho, nx, ny, x, y, &drx[c], &dry[c]);
+            stencil_grad(mu, nx, ny, p->walls != 0.0, x, y, &gmx, &gmy);
+            stencil_grad(rho, nx, ny, p->walls != 0.0, x, y, &drx[c], &dry[c]);
             Fx[c] = -rho[c] * gmx + p->fx;
             Fy[c] = -rho[c] * gmy + p->fy;
+            if (is_wall_row(p, y, ny)) {  /* mirrored neighbours: no normal gradient */
+                Fy[c] = p->fy;
+                dry[c] = 0.0;
+            }
+        }
+    if (p->walls != 0.0) wall_fill(p, nx, ny, f, Fx);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t c = (size_t)y * nx + x;
             double jx = 0.0, jy = 0.0;
             for (int i = 0; i < Q9; ++i) {
                 jx += f[(size_t)i * N + c] * CX[i];
@@ -398,7 +468,7 @@ static int fe_fields(const orc_params* p, int nx, int ny, const double* f, doubl
 }
 
 /* One IWB-FE-LBM step: Eq. (1) with Eq. (20) equilibrium, Eq. (21) forcing, C_i = 0. */
-static int fe_step(const orc_params* p, int nx, int ny, const double* f, double* fnew,
+static int fe_step(const orc_params* p, int nx, int ny, double* f, double* fnew,
                    double* rho, double* mu, double* Fx, double* Fy, double* ux, double* uy,
                    double* drx, double* dry) {
     size_t N = (size_t)nx * ny;
@@ -445,6 +515,7 @@ static int fe_step(const orc_params* p, int nx, int ny, const double* f, double*
                 double s = 0.0;
                 for (int k = 0; k < Q9; ++k) s += MINV[i][k] * dm[k];
                 int xd = wrap(x + CX[i], nx), yd = wrap(y + CY[i], ny);
+                if (p->walls != 0.0 && (y + CY[i] < 0 || y + CY[i] > ny - 1)) continue;  /* leaves through a wall */
                 fnew[(size_t)i * N + (size_t)yd * nx + xd] = fc[i] + s;
             }
         }
@@ -503,6 +574,13 @@ long orc_run(int model, const orc_params* p, int nx, int ny, double* f, long nst
         cur = nxt;
         nxt = t;
     }
+    if (p->walls != 0.0 && s == nsteps) {
+        /* complete the wall nodes' incoming populations of the returned state */
+        if (model == 0)
+            pp_fields(p, nx, ny, cur, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy);
+        else
+            fe_fields(p, nx, ny, cur, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy, w.drx, w.dry);
+    }
     if (cur != f) memcpy(f, cur, Q9 * N * sizeof(double));
     work_free(&w);
     return s;
@@ -519,8 +597,9 @@ int orc_macro(int model, const orc_params* p, int nx, int ny, const double* f, d
         work_free(&w);
         return -1;
     }
-    int rc = model == 0 ? pp_fields(p, nx, ny, f, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy)
-                        : fe_fields(p, nx, ny, f, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy, w.drx, w.dry);
+    memcpy(w.ftmp, f, Q9 * N * sizeof(double));  /* the wall fill writes the populations */
+    int rc = model == 0 ? pp_fields(p, nx, ny, w.ftmp, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy)
+                        : fe_fields(p, nx, ny, w.ftmp, w.rho, w.aux, w.Fx, w.Fy, w.ux, w.uy, w.drx, w.dry);
     if (rc == 0) {
         if (rho) memcpy(rho, w.rho, N * sizeof(double));
         if (ux) memcpy(ux, w.ux, N * sizeof(double));
@@ -600,8 +679,8 @@ void orc_q_tensor(const orc_params* p, const double* psi, int nx, int ny, int x,
 
 /* Stencils of Eq. (24) on a given field at (x, y): out = {d_x, d_y, lap}. */
 void orc_stencils(const double* phi, int nx, int ny, int x, int y, double* out) {
-    stencil_grad(phi, nx, ny, x, y, &out[0], &out[1]);
-    out[2] = stencil_lap(phi, nx, ny, x, y);
+    stencil_grad(phi, nx, ny, 0, x, y, &out[0], &out[1]);
+    out[2] = stencil_lap(phi, nx, ny, 0, x, y);
 }
 
 int orc_num_threads(void) {
