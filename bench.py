@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--sweep-lattices", type=int, default=512)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned calibration surrogate")
     ap.add_argument("--surrogate-sets", type=int, default=8000)
+    ap.add_argument("--no-walls", action="store_true", help="skip the walled-channel measurement")
     ap.add_argument("--plain-sets", type=int, default=6, help="held-out sets also calibrated one lattice at a time")
     return ap.parse_args()
 
@@ -242,6 +243,57 @@ def run_sweep(args):
             "strip_rows": info["strip_rows"],
             "workload": "512 seeded pseudopotential calibration lattices (64x4..512x512 slabs and droplets, "
                         "5e3-2e4 steps), FP32"}
+
+
+def run_walls(args, peak):
+    """Walled channel (no-slip walls on rows 0 and ny-1, body force): FP32 step throughput of
+    both models on a size x size plate channel (vapour below, liquid above, sine-perturbed
+    interface, F_x = 1e-6), CUDA events around 500 steps on the launching stream; and the
+    wall-clock rate of the 101 x 50 FP64 channel of Sec. 5.3 (steps/s over 2e4 steps)."""
+    import numpy as np
+    import torch
+
+    from paper_2403_11167_gb300 import inputs, lbm
+
+    size, nsteps = args.size, 500
+    out = {"workload": f"{size}x{size} plate channel, FP32, 500 steps per model; 101x50 Sec. 5.3 channel, FP64"}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for model, key in ((0, "pseudopotential"), (1, "free_energy")):
+            p = lbm.lbm_params_default(model, precision=lbm.LBM_F32, a=0.25, Tr=0.8, tau_nu=1.0, tau_e=1.0,
+                                       body_fx=1e-6)
+            ctx = lbm.Context(p, size, size, stream=stream, walls=True)
+            _, th = ctx.derived()
+            ctx.set_density(inputs.plate_channel(size, size, th.rho_v, th.rho_l, amp=8.0))
+            ctx.step(64)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.step(nsteps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s = e0.elapsed_time(e1) * 1e-3 / nsteps
+            gbs = BYTES_PER_CELL_F32 * size * size / s / 1e9
+            out[key] = {"mlups": size * size / s / 1e6, "us_per_launch": s * 1e6, "gbs_at_72B": gbs,
+                        "frac_of_hbm": gbs / peak, "kernel": ("pp_step_walls", "fe_step_walls")[model]}
+            ctx.close()
+        rates = {}
+        for model, key in ((0, "pseudopotential"), (1, "free_energy")):
+            kw = dict(a=0.25, Tr=0.8, tau_nu=1.0, tau_e=1.0, body_fx=1e-6)
+            kw.update({"match_kappa": 0.5} if model == 0 else {"kappa": 0.5})
+            p = lbm.lbm_params_default(model, precision=lbm.LBM_F64, **kw)
+            ctx = lbm.Context(p, 101, 50, stream=stream, walls=True)
+            _, th = ctx.derived()
+            ctx.set_density(inputs.plate_channel(101, 50, th.rho_v, th.rho_l))
+            ctx.step(640)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ctx.step(20000)
+            torch.cuda.synchronize()
+            rates[key] = 20000 / (time.perf_counter() - t)
+            ctx.close()
+        out["sec53_channel_f64_steps_per_s"] = rates
+    return out
 
 
 def run_surrogate(args):
@@ -463,6 +515,9 @@ def run_ours(args):
     surrogate = None
     if not args.no_surrogate:
         surrogate = run_surrogate(args)
+    walls = None
+    if not args.no_walls:
+        walls = run_walls(args, peak)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         v, cores, sample = oracle_mlups(rho0, args.cpu_seconds)
@@ -473,7 +528,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": args.steps * (2 + 2 * nsteps), "clocks": clocks, "per_model": per_model,
-        "sweep": sweep, "surrogate": surrogate,
+        "sweep": sweep, "surrogate": surrogate, "walls": walls,
         "kernel_source_sha256_12": kernel_source_hash(),
     }
     print(json.dumps(line))

@@ -43,7 +43,7 @@ extern "C" {
 /* status codes */
 #define LBM_OK 0
 #define LBM_ERR_ARG (-1)          /* invalid argument (size, tau <= 1/2, Tr outside (0,1), ...) */
-#define LBM_ERR_UNSUPPORTED (-2)  /* feature not built (walls, A != 0, ...) */
+#define LBM_ERR_UNSUPPORTED (-2)  /* feature not built (walls in x, A != 0, ...) */
 #define LBM_ERR_CUDA (-3)         /* a CUDA runtime call failed */
 #define LBM_ERR_DIVERGED (-4)     /* NaN/Inf or rho <= 0 seen; sticky for the context */
 #define LBM_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
@@ -130,8 +130,13 @@ int lbm_resolve_params_many(int n, const lbm_params* in, lbm_params* out, lbm_th
 /* Bytes of device workspace a context of this size and precision needs. */
 size_t lbm_workspace_bytes(int precision, int nx, int ny);
 
-/* Create a context for an nx x ny lattice (nx, ny >= 1; only periodic boundaries:
- * any other bc returns LBM_ERR_UNSUPPORTED).  stream: a cudaStream_t to run on, or
+/* Create a context for an nx x ny lattice (nx, ny >= 1).  Boundaries: bc_x must be
+ * LBM_BC_PERIODIC; bc_y is LBM_BC_PERIODIC or LBM_BC_WALL_ZOUHE, no-slip walls on the
+ * node rows 0 and ny-1 (needs ny >= 4), the parallel-plate channel of Sec. 5.3: Zou and
+ * He's condition completes a wall node's incoming populations so that its momentum is
+ * -F/2 (u = 0 including the half-force shift of Eq. 6b), and every stencil sees beyond
+ * a wall the row mirrored through it.  The body force body_fx/fy drives the flow.  Any
+ * other bc returns LBM_ERR_UNSUPPORTED.  stream: a cudaStream_t to run on, or
  * NULL for a stream the context creates and owns.  workspace: NULL to let the
  * library cudaMalloc its memory, or a device pointer (256-byte aligned) of at least
  * lbm_workspace_bytes(...) bytes that stays owned by the caller and must outlive

@@ -18,6 +18,7 @@
 #include "step_tma.cuh"
 #include "step_warp.cuh"
 #include "step_pair.cuh"
+#include "step_walls.cuh"
 #include "thermo.h"
 
 namespace {
@@ -102,6 +103,7 @@ struct lbm_ctx {
     double* d_obs;       // 8 doubles
     int* d_err;          // device error word of the TMA kernels (bounded waits)
     bool use_tma;
+    bool walls;          // no-slip walls on rows 0 and ny-1 (direct wall kernels)
     double* h_pinned;    // 8 doubles, pinned
     cudaStream_t stream;
     bool own_stream;
@@ -375,7 +377,9 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
     if (!p || nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31)) return LBM_ERR_ARG;
-    if (bc_x != LBM_BC_PERIODIC || bc_y != LBM_BC_PERIODIC) return LBM_ERR_UNSUPPORTED;
+    if (bc_x != LBM_BC_PERIODIC || (bc_y != LBM_BC_PERIODIC && bc_y != LBM_BC_WALL_ZOUHE)) return LBM_ERR_UNSUPPORTED;
+    const bool walls = bc_y == LBM_BC_WALL_ZOUHE;
+    if (walls && ny < 4) return LBM_ERR_ARG;
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ERR_ARG;
     int rc = lbm_resolve_params(p, &c->prm, &c->th);
@@ -391,6 +395,7 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     {
         const bool ppm = p->model == LBM_PSEUDOPOTENTIAL;
         const int tx = c->prec == LBM_F64 ? kTXd
+                       : walls ? kTXf
                        : ppm ? (kPPPair ? kPPPTX : kPPWarp ? kPPWTX : kTXf) : (kFEPair ? kFEPTX : kTXf);
         c->rows = choose_rows(nx, ny, tx, ppm ? 16 : 12);
     }
@@ -418,7 +423,8 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->partials = reinterpret_cast<double*>(c->ws + 2 * fbytes + align256(4 * n * c->esz));
     c->d_obs = reinterpret_cast<double*>(reinterpret_cast<char*>(c->partials) + align256(kRedBlocks * 3 * sizeof(double)));
     c->d_err = reinterpret_cast<int*>(reinterpret_cast<char*>(c->d_obs) + align256(8 * sizeof(double)));
-    c->use_tma = c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 4 && std::getenv("LBM_NO_TMA") == nullptr;
+    c->walls = walls;
+    c->use_tma = !walls && c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 4 && std::getenv("LBM_NO_TMA") == nullptr;
     cudaError_t e = cudaMallocHost(&c->h_pinned, 8 * sizeof(double));
     if (e != cudaSuccess) {
         if (c->own_ws) cudaFree(c->ws);
@@ -500,7 +506,23 @@ static int launch_step(lbm_ctx* c, int src) {
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
-    if (c->use_tma && pp && kPPPair) {
+    if (c->walls) {
+        if (c->prec == LBM_F32) {
+            dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
+            if (pp)
+                lbmk::pp_step_walls<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf);
+            else
+                lbmk::fe_step_walls<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf);
+        } else {
+            dim3 grid((c->nx + kTXd - 1) / kTXd, (c->ny + c->rows - 1) / c->rows);
+            if (pp)
+                lbmk::pp_step_walls<double, kTXd>
+                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd);
+            else
+                lbmk::fe_step_walls<double, kTXd>
+                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd);
+        }
+    } else if (c->use_tma && pp && kPPPair) {
         dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
         lbmk::pp_step_pair<kPPPWarps, kPPPStages><<<grid, (kPPPWarps + 1) * 32, sizeof(PPPSmem), c->stream>>>(
             (const float*)fin, (float*)fout, c->spf, c->d_err);
@@ -653,9 +675,20 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f) {
     return LBM_OK;
 }
 
+template <typename real>
+static int compute_fields(lbm_ctx* c, const lbmk::StepParams<real>& sp);
+
+// Walls: the stored state lacks the wall nodes' incoming populations until the fields pass
+// completes them (in place, in slots no step reads).
+static int complete_walls(lbm_ctx* c) {
+    if (!c->walls) return LBM_OK;
+    return c->prec == LBM_F32 ? compute_fields(c, c->spf) : compute_fields(c, c->spd);
+}
+
 extern "C" int lbm_get_populations(lbm_ctx* c, double* f) {
     if (!c || !f) return LBM_ERR_ARG;
     if (!c->ready) return LBM_ERR_STATE;
+    if (int rc = complete_walls(c)) return rc;
     const size_t n = (size_t)c->nx * c->ny;
     std::vector<char> stage(n * c->esz);
     CK(cudaStreamSynchronize(c->stream));
@@ -678,6 +711,7 @@ extern "C" int lbm_get_populations_at(lbm_ctx* c, int n, const int* xs, const in
     if (!c->ready) return LBM_ERR_STATE;
     for (int k = 0; k < n; ++k)
         if (xs[k] < 0 || xs[k] >= c->nx || ys[k] < 0 || ys[k] >= c->ny) return LBM_ERR_ARG;
+    if (int rc = complete_walls(c)) return rc;
     CK(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < n; ++k)
         for (int i = 0; i < 9; ++i) {
@@ -712,6 +746,15 @@ static int compute_fields(lbm_ctx* c, const lbmk::StepParams<real>& sp) {
     real* uy = ux + n;
     const real* f = static_cast<const real*>(c->f[c->cur]);
     const int model = c->prm.model;
+    if (c->walls) {
+        real* fw = static_cast<real*>(c->f[c->cur]);
+        lbmk::rho_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, sp, model);
+        if (model == LBM_FREE_ENERGY) lbmk::mu_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
+        lbmk::walls_complete_kernel<real><<<(2 * c->nx + 255) / 256, 256, 0, c->stream>>>(fw, rho, aux, sp, model);
+        lbmk::velocity_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, ux, uy, sp, model);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
     lbmk::rho_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(f, rho, aux, sp, model);
     if (model == LBM_FREE_ENERGY) lbmk::mu_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
     lbmk::velocity_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(f, rho, aux, ux, uy, sp, model);

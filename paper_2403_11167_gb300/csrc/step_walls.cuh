@@ -1,0 +1,375 @@
+// step_walls.cuh -- the time step and the field kernels of a channel bounded by no-slip
+// walls on rows 0 and ny-1 (periodic in x): the two-phase flow between parallel plates of
+// Sec. 5.3, driven by the constant body force of StepParams::fx, fy.
+//
+// Wall treatment (Zou and He's velocity condition, cited in Sec. 5.3):
+//   * a wall node lacks the populations that would stream in from beyond the wall (bottom:
+//     i = 2, 5, 6; top: i = 4, 7, 8).  They are set so that the node momentum is J = -F/2,
+//     i.e. u = 0 including the half-force shift of Eq. (6b) (wall_fill);
+//   * every stencil (psi, rho, mu and their gradients / Laplacian) sees beyond a wall the
+//     row mirrored through it (row -1 is row 1, row ny is row ny-2).  The wall-normal
+//     component of each central-difference gradient is then exactly zero, so a wall node's
+//     normal force is the body force alone and its density, sum_i f_i, depends on J_y only:
+//     a first fill with J = (0, -fy/2) fixes rho, psi and mu; after the forces are known the
+//     fill is repeated with J_x = -F_x/2 before the collision.
+//   * populations that stream out through a wall are dropped: in the pull layout (a buffer
+//     holds S_i(y) = f_i(y + c_i)) their slots are exactly the slots a wall node pulls its
+//     unknowns from, which the fill overwrites.
+//
+// The kernels follow the direct step kernels of lbm_kernels.cuh (one column per thread,
+// shared-memory rings of the neighbour fields, one halo warp); the pulled rows map through
+// mirror_row, wall rows get the two fills, and a wall row's collision sees its neighbour
+// fields mirrored.  Requirements (checked on the host): ny >= 4.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.cuh"
+
+namespace lbmk {
+
+// Row seen by a stencil: rows beyond a wall are mirrored through the wall node.
+__host__ __device__ __forceinline__ int mirror_row(int y, int ny) {
+    return y < 0 ? -y : (y > ny - 1 ? 2 * (ny - 1) - y : y);
+}
+
+// Zou-He completion of a wall node for the node momentum (Jx, Jy):
+//   bottom  f2 = f4 + 2/3 Jy,  f5 = f7 - (f1 - f3)/2 + Jx/2 + Jy/6,  f6 = f8 + (f1 - f3)/2 - Jx/2 + Jy/6
+//   top     f4 = f2 - 2/3 Jy,  f7 = f5 + (f1 - f3)/2 - Jx/2 - Jy/6,  f8 = f6 - (f1 - f3)/2 + Jx/2 - Jy/6
+// (sum_i f_i c_i = J follows from these and the known populations).
+template <typename real>
+__device__ __forceinline__ void wall_fill(real v[9], bool top, real Jx, real Jy) {
+    const real h = real(0.5) * (v[1] - v[3]);
+    const real hx = real(0.5) * Jx, sy = Jy * real(1.0 / 6.0), ty = Jy * real(2.0 / 3.0);
+    if (!top) {
+        v[2] = v[4] + ty;
+        v[5] = (v[7] - h) + (hx + sy);
+        v[6] = (v[8] + h) - (hx - sy);
+    } else {
+        v[4] = v[2] - ty;
+        v[7] = (v[5] + h) - (hx + sy);
+        v[8] = (v[6] - h) + (hx - sy);
+    }
+}
+
+// Neighbour values n[i] at x + c_i of a wall node with the rows beyond the wall replaced by
+// their mirror images (bottom: 4 <- 2, 7 <- 6, 8 <- 5; top: 2 <- 4, 5 <- 8, 6 <- 7).
+template <typename real>
+__device__ __forceinline__ void mirror_neighbours(real n[9], bool top) {
+    if (!top) {
+        n[4] = n[2];
+        n[7] = n[6];
+        n[8] = n[5];
+    } else {
+        n[2] = n[4];
+        n[5] = n[8];
+        n[6] = n[7];
+    }
+}
+
+// x component of the Eq. (24) gradient weights (sum_i w_i phi_i c_ix / c_s^2), as in the
+// collision functions.
+template <typename real>
+__device__ __forceinline__ real grad_x(const real n[9]) {
+    return (n[1] - n[3]) * real(1.0 / 3.0) + ((n[5] - n[7]) + (n[8] - n[6])) * real(1.0 / 12.0);
+}
+
+// Pulled populations of row y (already mirrored) of column x; a wall row gets the first
+// fill, J = (0, -fy/2).  The pull of a wall row reads its unknowns from the wrapped row:
+// in bounds, and overwritten by the fill.
+template <typename real>
+__device__ __forceinline__ void pull_row_walls(const real* __restrict__ f, const StepParams<real>& P, int x, int xm,
+                                               int xp, int y, real v[9]) {
+    const int ny = P.ny, nx = P.nx;
+    const long long om = (long long)(y == 0 ? ny - 1 : y - 1) * nx, o0 = (long long)y * nx,
+                    op = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
+    pull9(f, P.pitch, x, xm, xp, om, o0, op, v);
+    if (y == 0 || y == ny - 1) wall_fill(v, y != 0, real(0), real(-0.5) * P.fy);
+}
+
+// ---------------------------------------------------------------------------------
+// Pseudopotential step between walls (Eqs. 1, 4, 6, 10, 11, 13, 30-32).
+template <typename real, int TX>
+__global__ void __launch_bounds__(TX + 32) pp_step_walls(const real* __restrict__ fin, real* __restrict__ fout,
+                                                         const StepParams<real> P) {
+    __shared__ real s_psi[4][TX + 2];
+    const int nx = P.nx, ny = P.ny;
+    const long long pitch = P.pitch;
+    const int x0 = blockIdx.x * TX;
+    const int w = min(TX, nx - x0);
+    const int y0 = blockIdx.y * P.rows;
+    const int y1 = min(y0 + P.rows, ny);
+    const int t = threadIdx.x;
+    const bool is_main = t < TX;
+    bool has_col;
+    int x, sc;
+    if (is_main) {
+        has_col = t < w;
+        x = x0 + (has_col ? t : 0);
+        sc = t + 1;
+    } else {
+        const int lane = t - TX;
+        has_col = lane < 2;
+        x = lane == 0 ? wrap_idx(x0 - 1, nx) : wrap_idx(x0 + w, nx);
+        sc = lane == 0 ? 0 : w + 1;
+    }
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+
+    real cur[9], prv[9];
+    real rho_cur = real(1), rho_prv = real(1);
+    if (has_col) {
+        pull_row_walls(fin, P, x, xm, xp, mirror_row(y0 - 1, ny), cur);
+        rho_cur = sum9(cur);
+    }
+#pragma unroll 1
+    for (int r = y0 - 1; r <= y1; ++r) {
+        real nxt[9];
+        real rho_nxt = real(1);
+        if (has_col && r < y1) {
+            pull_row_walls(fin, P, x, xm, xp, mirror_row(r + 1, ny), nxt);
+            rho_nxt = sum9(nxt);
+        }
+        if (has_col) s_psi[r & 3][sc] = pseudo_psi(rho_cur, P);
+        __syncthreads();
+        if (is_main && has_col && r > y0) {
+            // centre row c = r - 1: neighbours in rows c-1 (slot r-2), c (r-1), c+1 (r)
+            const int c = r - 1;
+            const real* sm = s_psi[(r - 2) & 3];
+            const real* s0 = s_psi[(r - 1) & 3];
+            const real* sp = s_psi[r & 3];
+            real pn[9];
+            pn[0] = s0[sc];
+            pn[1] = s0[sc + 1];
+            pn[2] = sp[sc];
+            pn[3] = s0[sc - 1];
+            pn[4] = sm[sc];
+            pn[5] = sp[sc + 1];
+            pn[6] = sp[sc - 1];
+            pn[7] = sm[sc - 1];
+            pn[8] = sm[sc + 1];
+            if (c == 0 || c == ny - 1) {
+                mirror_neighbours(pn, c != 0);
+                const real Fx = pn[0] * grad_x(pn) + P.fx;  // F_int,x + body force (Eq. 10)
+                wall_fill(prv, c != 0, real(-0.5) * Fx, real(-0.5) * P.fy);
+            }
+            pp_collide(prv, rho_prv, pn[0], pn, P);
+            const long long o = (long long)c * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fout[i * pitch + o] = prv[i];
+        }
+        if (has_col) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                prv[i] = cur[i];
+                cur[i] = nxt[i];
+            }
+            rho_prv = rho_cur;
+            rho_cur = rho_nxt;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Free-energy step between walls (Eqs. 1, 6, 20, 21, 24, 29).  Rings as in fe_step_kernel:
+// rho (8 rows, 2 halo columns each side), mu (4 rows, 1 halo column).
+template <typename real, int TX>
+__global__ void __launch_bounds__(TX + 32) fe_step_walls(const real* __restrict__ fin, real* __restrict__ fout,
+                                                         const StepParams<real> P) {
+    __shared__ real s_rho[8][TX + 4];
+    __shared__ real s_mu[4][TX + 2];
+    const int nx = P.nx, ny = P.ny;
+    const long long pitch = P.pitch;
+    const int x0 = blockIdx.x * TX;
+    const int w = min(TX, nx - x0);
+    const int y0 = blockIdx.y * P.rows;
+    const int y1 = min(y0 + P.rows, ny);
+    const int t = threadIdx.x;
+    const bool is_main = t < TX;
+    bool has_col, has_mu;
+    int x, rc, mc;  // global column, rho-ring column, mu-ring column
+    if (is_main) {
+        has_col = t < w;
+        has_mu = has_col;
+        x = x0 + (has_col ? t : 0);
+        rc = t + 2;
+        mc = t + 1;
+    } else {
+        const int lane = t - TX;
+        has_col = lane < 4;
+        has_mu = lane == 1 || lane == 2;
+        const int off = lane == 0 ? -2 : lane == 1 ? -1 : lane == 2 ? w : w + 1;
+        x = wrap_idx(x0 + off, nx);
+        rc = lane == 0 ? 0 : lane == 1 ? 1 : lane == 2 ? w + 2 : w + 3;
+        mc = lane == 1 ? 0 : w + 1;
+    }
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+    real p0[9], p1[9], p2[9];  // pulled populations of rows r-2, r-1, r
+    if (has_col) pull_row_walls(fin, P, x, xm, xp, mirror_row(y0 - 2, ny), p2);
+#pragma unroll 1
+    for (int r = y0 - 2; r <= y1 + 1; ++r) {
+        real nxt[9];
+        if (has_col && r <= y1) pull_row_walls(fin, P, x, xm, xp, mirror_row(r + 1, ny), nxt);
+        if (has_col) s_rho[r & 7][rc] = sum9(p2);
+        __syncthreads();
+        if (has_mu && r >= y0) {
+            // mu at row r - 1 from rho rows r-2, r-1, r (mirrored rows hold mirrored rho)
+            const real* rm = s_rho[(r - 2) & 7];
+            const real* r0 = s_rho[(r - 1) & 7];
+            const real* rp = s_rho[r & 7];
+            real rn[9];
+            rn[1] = r0[rc + 1];
+            rn[2] = rp[rc];
+            rn[3] = r0[rc - 1];
+            rn[4] = rm[rc];
+            rn[5] = rp[rc + 1];
+            rn[6] = rp[rc - 1];
+            rn[7] = rm[rc - 1];
+            rn[8] = rm[rc + 1];
+            s_mu[(r - 1) & 3][mc] = fe_mu(r0[rc], rn, P);
+        }
+        __syncthreads();
+        if (is_main && has_col && r >= y0 + 2) {
+            // centre row c = r - 2
+            const int c = r - 2;
+            const real* mm = s_mu[(r - 3) & 3];
+            const real* m0 = s_mu[(r - 2) & 3];
+            const real* mp = s_mu[(r - 1) & 3];
+            const real* rm = s_rho[(r - 3) & 7];
+            const real* r0 = s_rho[(r - 2) & 7];
+            const real* rp = s_rho[(r - 1) & 7];
+            real mn[9], rn[9];
+            mn[1] = m0[mc + 1]; mn[2] = mp[mc]; mn[3] = m0[mc - 1]; mn[4] = mm[mc];
+            mn[5] = mp[mc + 1]; mn[6] = mp[mc - 1]; mn[7] = mm[mc - 1]; mn[8] = mm[mc + 1];
+            rn[1] = r0[rc + 1]; rn[2] = rp[rc]; rn[3] = r0[rc - 1]; rn[4] = rm[rc];
+            rn[5] = rp[rc + 1]; rn[6] = rp[rc - 1]; rn[7] = rm[rc - 1]; rn[8] = rm[rc + 1];
+            const real rho_c = r0[rc];
+            if (c == 0 || c == ny - 1) {
+                // mu beyond the wall is mu of the mirrored row (the ring holds the value
+                // recomputed from mirrored rho, equal up to rounding order)
+                mirror_neighbours(mn, c != 0);
+                mirror_neighbours(rn, c != 0);
+                const real Fx = -rho_c * grad_x(mn) + P.fx;  // F = -rho grad mu + body force
+                wall_fill(p0, c != 0, real(-0.5) * Fx, real(-0.5) * P.fy);
+            }
+            fe_collide(p0, rho_c, mn, rn, P);
+            const long long o = (long long)c * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
+        }
+        if (has_col) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                p0[i] = p1[i];
+                p1[i] = p2[i];
+                p2[i] = nxt[i];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Fields of the current state of a walled channel (observables, not on the step path).
+
+// Values at x + c_i with rows beyond a wall mirrored; n[0] is the cell itself.
+template <typename real>
+__device__ __forceinline__ void gather8_walls(const real* __restrict__ a, int x, int y, int nx, int ny, real n[9]) {
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const long long ym = (long long)mirror_row(y - 1, ny) * nx, y0 = (long long)y * nx,
+                    yp = (long long)mirror_row(y + 1, ny) * nx;
+    n[0] = a[y0 + x];
+    n[1] = a[y0 + xp];
+    n[2] = a[yp + x];
+    n[3] = a[y0 + xm];
+    n[4] = a[ym + x];
+    n[5] = a[yp + xp];
+    n[6] = a[yp + xm];
+    n[7] = a[ym + xm];
+    n[8] = a[ym + xp];
+}
+
+// rho (Eq. 6a, wall rows after the first fill) and aux = psi (P) or rho (FE).
+template <typename real>
+__global__ void rho_walls_kernel(const real* __restrict__ f, real* __restrict__ rho, real* __restrict__ aux,
+                                 const StepParams<real> P, int model) {
+    const long long n = (long long)P.nx * P.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % P.nx), y = (int)(c / P.nx);
+        real v[9];
+        pull_row_walls(f, P, x, x == 0 ? P.nx - 1 : x - 1, x == P.nx - 1 ? 0 : x + 1, y, v);
+        const real r = sum9(v);
+        rho[c] = r;
+        aux[c] = model == 0 ? pseudo_psi(r, P) : r;
+    }
+}
+
+// FE: mu from rho with mirrored rows (writes into mu).
+template <typename real>
+__global__ void mu_walls_kernel(const real* __restrict__ rho, real* __restrict__ mu, const StepParams<real> P) {
+    const long long n = (long long)P.nx * P.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        real rn[9];
+        gather8_walls(rho, (int)(c % P.nx), (int)(c / P.nx), P.nx, P.ny, rn);
+        mu[c] = fe_mu(rn[0], rn, P);
+    }
+}
+
+// Completes the wall nodes of the stored state: the final fill (J = -F/2) of each wall node,
+// written into the slots its unknowns are pulled from (the dropped outgoing populations),
+// so that pulling any cell returns the full state.  Each thread reads and writes only its
+// own node's unknown slots.  aux = psi (P) or mu (FE).
+template <typename real>
+__global__ void walls_complete_kernel(real* __restrict__ f, const real* __restrict__ rho,
+                                      const real* __restrict__ aux, const StepParams<real> P, int model) {
+    const int nx = P.nx, ny = P.ny;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * nx; k += gridDim.x * blockDim.x) {
+        const bool top = k >= nx;
+        const int x = top ? k - nx : k, y = top ? ny - 1 : 0;
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        real v[9], an[9];
+        pull_row_walls(f, P, x, xm, xp, y, v);
+        gather8_walls(aux, x, y, nx, ny, an);
+        const long long c = (long long)y * nx + x;
+        const real Fx = (model == 0 ? an[0] : -rho[c]) * grad_x(an) + P.fx;
+        wall_fill(v, top, real(-0.5) * Fx, real(-0.5) * P.fy);
+        // f_i(x, y) = S_i(x - c_i): bottom unknowns 2 (0,1), 5 (1,1), 6 (-1,1) sit in row ny-1;
+        // top unknowns 4 (0,-1), 7 (-1,-1), 8 (1,-1) in row 0
+        const long long ro = top ? 0 : (long long)(ny - 1) * nx;
+        if (!top) {
+            f[2 * P.pitch + ro + x] = v[2];
+            f[5 * P.pitch + ro + xm] = v[5];
+            f[6 * P.pitch + ro + xp] = v[6];
+        } else {
+            f[4 * P.pitch + ro + x] = v[4];
+            f[7 * P.pitch + ro + xp] = v[7];
+            f[8 * P.pitch + ro + xm] = v[8];
+        }
+    }
+}
+
+// u of Eq. (6b) of the completed state, mirrored neighbour fields (the wall-normal interaction
+// force vanishes at wall nodes, so u = 0 there up to rounding).
+template <typename real>
+__global__ void velocity_walls_kernel(const real* __restrict__ f, const real* __restrict__ rho,
+                                      const real* __restrict__ aux, real* __restrict__ ux, real* __restrict__ uy,
+                                      const StepParams<real> P, int model) {
+    const long long n = (long long)P.nx * P.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % P.nx), y = (int)(c / P.nx);
+        real v[9], an[9];
+        pull_cell(f, P.pitch, x, y, P.nx, P.ny, v);
+        gather8_walls(aux, x, y, P.nx, P.ny, an);
+        const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
+        const real gx = (an[1] - an[3]) * w1 + ((an[5] - an[7]) + (an[8] - an[6])) * w2;
+        const real gy = (an[2] - an[4]) * w1 + ((an[5] - an[7]) + (an[6] - an[8])) * w2;
+        const real r = rho[c];
+        const real s = model == 0 ? an[0] : -r;
+        const real Fx = s * gx + P.fx, Fy = s * gy + P.fy;
+        const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+        const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+        ux[c] = (jx + real(0.5) * Fx) / r;
+        uy[c] = (jy + real(0.5) * Fy) / r;
+    }
+}
+
+}  // namespace lbmk

@@ -13,6 +13,10 @@ Recipes (the paper initialises every run from f = f^eq(rho0, u = 0), Secs. 5.3-5
 * ``spinodal_noise`` -- rho = rho_mean (1 + U(-amp, amp)), i.i.d. per cell from
   NumPy's PCG64 with the given seed (spinodal decomposition from a uniform state).
 * ``random_field`` -- i.i.d. uniform densities in [lo, hi] (brute-force checks).
+* ``plate_channel`` -- the parallel-plate channel of Sec. 5.3: vapour in the bottom half,
+  liquid in the top half, rho(x, y) = rho_v + (rho_l - rho_v)/2 [1 + tanh(2(y - h(x))/W0)]
+  with the interface at h(x) = (ny - 1)/2 + amp sin(2 pi x / nx) (amp = 0: the paper's flat
+  interface; amp > 0 gives parity runs x-gradients).
 """
 import numpy as np
 
@@ -38,6 +42,12 @@ def spinodal_noise(nx: int, ny: int, rho_mean: float, amp: float = 0.01, seed: i
 def random_field(nx: int, ny: int, lo: float, hi: float, seed: int = 0) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(lo, hi, size=(ny, nx))
+
+
+def plate_channel(nx: int, ny: int, rho_v: float, rho_l: float, w0: float = 5.0, amp: float = 0.0) -> np.ndarray:
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    h = (ny - 1) / 2.0 + amp * np.sin(2.0 * np.pi * xx / nx)
+    return rho_v + 0.5 * (rho_l - rho_v) * (1.0 + np.tanh(2.0 * (yy - h) / w0))
 
 
 def calibration_sweep(n: int = 512, seed: int = 11167, step_range=(5000, 20000), w0: float = 5.0):

@@ -34,6 +34,7 @@ LBM_FREE_ENERGY = 1
 LBM_F32 = 0
 LBM_F64 = 1
 LBM_BC_PERIODIC = 0
+LBM_BC_WALL_ZOUHE = 1
 FLAT = 0
 DROPLET = 1
 
@@ -218,7 +219,8 @@ class Context:
     """Owner of one ``lbm_ctx``.  The workspace is a torch uint8 CUDA tensor and the
     stream a torch stream (its handle is passed to the library)."""
 
-    def __init__(self, params: lbm_params, nx: int, ny: int, stream=None, device="cuda"):
+    def __init__(self, params: lbm_params, nx: int, ny: int, stream=None, device="cuda", walls: bool = False):
+        """walls: no-slip walls on rows 0 and ny-1 (Zou-He), else periodic in y."""
         import torch
 
         self.nx, self.ny = nx, ny
@@ -229,7 +231,8 @@ class Context:
         aligned = (base + 255) & ~255
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         handle = ctypes.c_void_p()
-        rc = _lib().lbm_create(ctypes.byref(params), nx, ny, LBM_BC_PERIODIC, LBM_BC_PERIODIC,
+        rc = _lib().lbm_create(ctypes.byref(params), nx, ny, LBM_BC_PERIODIC,
+                               LBM_BC_WALL_ZOUHE if walls else LBM_BC_PERIODIC,
                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.c_void_p(aligned),
                                ctypes.c_size_t(nbytes), ctypes.byref(handle))
         _check(rc, "lbm_create")

@@ -4,19 +4,20 @@ import numpy as np
 import oracle as O
 
 
-def oracle_params(rp, th):
-    """Oracle parameters equal to a resolved ``lbm_params`` (rp) and its thermodynamics (th)."""
+def oracle_params(rp, th, walls=False):
+    """Oracle parameters equal to a resolved ``lbm_params`` (rp) and its thermodynamics (th);
+    walls: no-slip walls on rows 0 and ny-1."""
     return O.make_params(a=rp.a, b=rp.b, R=rp.R, T=th.T, tau_rho=1.0, tau_e=rp.tau_e, tau_zeta=rp.tau_zeta,
                          tau_q=rp.tau_q, tau_j=rp.tau_j, tau_nu=rp.tau_nu, kappa_P=rp.kappa_P,
                          kappa_Li=rp.kappa_Li, sigma_Li=rp.sigma_Li, kappa=rp.kappa, fx=rp.body_fx,
-                         fy=rp.body_fy)
+                         fy=rp.body_fy, walls=1.0 if walls else 0.0)
 
 
-def gpu_context(model, precision, nx, ny, **kw):
+def gpu_context(model, precision, nx, ny, walls=False, **kw):
     from paper_2403_11167_gb300 import lbm
 
     p = lbm.lbm_params_default(model, precision=precision, **kw)
-    ctx = lbm.Context(p, nx, ny)
+    ctx = lbm.Context(p, nx, ny, walls=walls)
     rp, th = ctx.derived()
     return ctx, rp, th
 

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from oracle import thermo
+from oracle import plate, thermo
 
 A, TAU = 0.25, 1.0
 
@@ -29,13 +29,44 @@ def _run(model, ny, steps, Tr, fx, rho_col):
 
 
 def _s89(rho_col, fx):
-    """Eq. (89) with mu(y) = rho(y) c_s^2 (tau - 1/2), no slip at y = 0 and y = H (trapezoid
-    rule on the lattice nodes)."""
-    y = np.arange(len(rho_col), dtype=float)
-    mu = rho_col / 3.0 * (TAU - 0.5)
-    i1 = np.concatenate([[0.0], np.cumsum(0.5 * (y[1:] / mu[1:] + y[:-1] / mu[:-1]))])
-    i0 = np.concatenate([[0.0], np.cumsum(0.5 * (1 / mu[1:] + 1 / mu[:-1]))])
-    return -fx * i1 + fx * i1[-1] / i0[-1] * i0
+    """Eq. (89) on the lattice nodes: plates on the wall rows, H = ny - 1."""
+    return plate.s89(np.arange(len(rho_col), dtype=float), plate.viscosity(rho_col, TAU), fx)
+
+
+def test_s88_reduces_to_poiseuille_and_matches_at_the_interface():
+    """Eq. (88): equal viscosities give F y (H - y)/(2 mu); otherwise no slip at both plates
+    and continuity of u and of mu du/dy at y = H/2 (one-sided differences)."""
+    H, fx = 49.0, 1e-6
+    y = np.linspace(0, H, 99)
+    assert np.abs(plate.s88(y, H, 0.1, 0.1, fx) - fx * y * (H - y) / 0.2).max() < 1e-15
+    mu1, mu2 = 0.01, 0.13
+    assert abs(plate.s88(0.0, H, mu1, mu2, fx)) < 1e-16 and abs(plate.s88(H, H, mu1, mu2, fx)) < 1e-16
+    e = 1e-6
+    lo, mid, hi = plate.s88([H / 2 - e, H / 2, H / 2 + e], H, mu1, mu2, fx)
+    assert abs(lo - mid) < 1e-6 * abs(mid) and abs(hi - mid) < 1e-6 * abs(mid)
+    d1 = mu1 * (mid - plate.s88(H / 2 - 1e-4, H, mu1, mu2, fx)) / 1e-4
+    d2 = mu2 * (plate.s88(H / 2 + 1e-4, H, mu1, mu2, fx) - mid) / 1e-4
+    assert abs(d1 - d2) < 1e-4 * abs(d1)  # one-sided differences: O(F_x h) = 1e-10
+    # each branch solves mu u'' = -F_x (second differences away from the interface)
+    for yy, mu in ((10.0, mu1), (40.0, mu2)):
+        u = plate.s88([yy - 0.5, yy, yy + 0.5], H, mu1, mu2, fx)
+        assert abs(mu * (u[0] - 2 * u[1] + u[2]) / 0.25 + fx) < 1e-9 * fx
+
+
+def test_s89_reduces_to_poiseuille_and_converges_to_s88():
+    """Eq. (89): exact (trapezoid rule on linear integrands) for uniform viscosity; for a
+    viscosity step at H/2 it tends to Eq. (88) as the nodes refine."""
+    H, fx = 49.0, 1e-6
+    y = np.linspace(0, H, 50)
+    assert np.abs(plate.s89(y, np.full(50, 0.1), fx) - fx * y * (H - y) / 0.2).max() < 1e-15
+    mu1, mu2 = 0.01, 0.13
+    errs = []
+    for n in (1001, 4001):
+        yy = np.linspace(0, H, n)
+        mu = np.where(yy <= H / 2, mu1, mu2)
+        ref = plate.s88(yy, H, mu1, mu2, fx)
+        errs.append(np.abs(plate.s89(yy, mu, fx) - ref).max() / ref.max())
+    assert errs[1] < 0.3 * errs[0] and errs[1] < 2e-3
 
 
 @pytest.mark.parametrize("model", [O.PP, O.FE])
