@@ -247,7 +247,8 @@ def run_sweep(args):
 
 def run_walls(args, peak):
     """Walled channel (no-slip walls on rows 0 and ny-1, body force): FP32 step throughput of
-    both models on a size x size plate channel (vapour below, liquid above, sine-perturbed
+    both models (periodic strip kernel on the whole lattice, then the wall bands recomputed by
+    the wall kernel; two launches per step) on a size x size plate channel (vapour below, liquid above, sine-perturbed
     interface, F_x = 1e-6), CUDA events around 500 steps on the launching stream; and the
     wall-clock rate of the 101 x 50 FP64 channel of Sec. 5.3 (steps/s over 2e4 steps)."""
     import numpy as np
@@ -275,7 +276,9 @@ def run_walls(args, peak):
             s = e0.elapsed_time(e1) * 1e-3 / nsteps
             gbs = BYTES_PER_CELL_F32 * size * size / s / 1e9
             out[key] = {"mlups": size * size / s / 1e6, "us_per_launch": s * 1e6, "gbs_at_72B": gbs,
-                        "frac_of_hbm": gbs / peak, "kernel": ("pp_step_walls", "fe_step_walls")[model]}
+                        "frac_of_hbm": gbs / peak,
+                        "kernels": ("pp_step_pair + pp_step_walls (wall bands, 2 rows)",
+                                    "fe_step_pair + fe_step_walls (wall bands, 3 rows)")[model]}
             ctx.close()
         rates = {}
         for model, key in ((0, "pseudopotential"), (1, "free_energy")):

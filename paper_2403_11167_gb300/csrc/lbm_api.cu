@@ -44,6 +44,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 #endif
 constexpr int kTXf = LBM_TXF;  // columns per CTA, FP32
 constexpr int kTXd = 64;   // columns per CTA, FP64
+constexpr int kWallBandPP = 2;  // rows next to each wall that a periodic step gets wrong
+constexpr int kWallBandFE = 3;
 constexpr int kGraphSteps = 64;
 constexpr int kRedBlocks = 304;  // observables partial-reduction blocks (2 x 152 SMs)
 constexpr int kTmaStages = LBM_TMA_STAGES;  // row-pipeline depth of the TMA-fed FP32 kernels
@@ -394,8 +396,10 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->pitch = plane_pitch(nx, ny);
     {
         const bool ppm = p->model == LBM_PSEUDOPOTENTIAL;
+        const bool fast = c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 2 * kWallBandFE &&
+                          kPPPair && kFEPair && std::getenv("LBM_NO_TMA") == nullptr;
         const int tx = c->prec == LBM_F64 ? kTXd
-                       : walls ? kTXf
+                       : (walls && !fast) ? kTXf
                        : ppm ? (kPPPair ? kPPPTX : kPPWarp ? kPPWTX : kTXf) : (kFEPair ? kFEPTX : kTXf);
         c->rows = choose_rows(nx, ny, tx, ppm ? 16 : 12);
     }
@@ -424,7 +428,8 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->d_obs = reinterpret_cast<double*>(reinterpret_cast<char*>(c->partials) + align256(kRedBlocks * 3 * sizeof(double)));
     c->d_err = reinterpret_cast<int*>(reinterpret_cast<char*>(c->d_obs) + align256(8 * sizeof(double)));
     c->walls = walls;
-    c->use_tma = !walls && c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 4 && std::getenv("LBM_NO_TMA") == nullptr;
+    // walls: the periodic strip kernels serve the interior when both wall bands fit
+    c->use_tma = (!walls || (kPPPair && kFEPair && ny >= 2 * kWallBandFE)) && c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 4 && std::getenv("LBM_NO_TMA") == nullptr;
     cudaError_t e = cudaMallocHost(&c->h_pinned, 8 * sizeof(double));
     if (e != cudaSuccess) {
         if (c->own_ws) cudaFree(c->ws);
@@ -506,21 +511,37 @@ static int launch_step(lbm_ctx* c, int src) {
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
-    if (c->walls) {
+    if (c->walls && c->use_tma) {
+        // periodic fast step over the whole lattice, then the wall bands recomputed
+        const int band = pp ? kWallBandPP : kWallBandFE;
+        if (pp) {
+            dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
+            lbmk::pp_step_pair<kPPPWarps, kPPPStages><<<grid, (kPPPWarps + 1) * 32, sizeof(PPPSmem), c->stream>>>(
+                (const float*)fin, (float*)fout, c->spf, c->d_err);
+            lbmk::pp_step_walls<float, kTXf><<<dim3((c->nx + kTXf - 1) / kTXf, 2), kTXf + 32, 0, c->stream>>>(
+                (const float*)fin, (float*)fout, c->spf, band);
+        } else {
+            dim3 grid((c->nx + kFEPTX - 1) / kFEPTX, (c->ny + c->rows - 1) / c->rows);
+            lbmk::fe_step_pair<kFEPWarps, kFEPStages><<<grid, (kFEPWarps + 1) * 32, sizeof(FEPSmem), c->stream>>>(
+                (const float*)fin, (float*)fout, c->spf, c->d_err);
+            lbmk::fe_step_walls<float, kTXf><<<dim3((c->nx + kTXf - 1) / kTXf, 2), kTXf + 32, 0, c->stream>>>(
+                (const float*)fin, (float*)fout, c->spf, band);
+        }
+    } else if (c->walls) {
         if (c->prec == LBM_F32) {
             dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
             if (pp)
-                lbmk::pp_step_walls<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf);
+                lbmk::pp_step_walls<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0);
             else
-                lbmk::fe_step_walls<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf);
+                lbmk::fe_step_walls<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0);
         } else {
             dim3 grid((c->nx + kTXd - 1) / kTXd, (c->ny + c->rows - 1) / c->rows);
             if (pp)
                 lbmk::pp_step_walls<double, kTXd>
-                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd);
+                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0);
             else
                 lbmk::fe_step_walls<double, kTXd>
-                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd);
+                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0);
         }
     } else if (c->use_tma && pp && kPPPair) {
         dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);

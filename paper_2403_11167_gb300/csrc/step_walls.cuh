@@ -20,6 +20,14 @@
 // shared-memory rings of the neighbour fields, one halo warp); the pulled rows map through
 // mirror_row, wall rows get the two fills, and a wall row's collision sees its neighbour
 // fields mirrored.  Requirements (checked on the host): ny >= 4.
+//
+// band > 0 launches only the rows next to the walls: grid.y = 2, CTA row 0 updates rows
+// [0, band), CTA row 1 rows [ny - band, ny).  This completes a step whose interior was
+// updated by a periodic step kernel: a periodic stencil is exact on every row whose
+// neighbourhood holds neither a wall row (whose density needs the fill) nor a row beyond
+// the wall (mirrored, not wrapped).  The pseudopotential collision reads psi one row away
+// (rows 0 and 1 differ, band = 2); the free-energy collision reads mu one row away and mu
+// reads rho one row further (rows 0, 1, 2 differ, band = 3).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -90,14 +98,14 @@ __device__ __forceinline__ void pull_row_walls(const real* __restrict__ f, const
 // Pseudopotential step between walls (Eqs. 1, 4, 6, 10, 11, 13, 30-32).
 template <typename real, int TX>
 __global__ void __launch_bounds__(TX + 32) pp_step_walls(const real* __restrict__ fin, real* __restrict__ fout,
-                                                         const StepParams<real> P) {
+                                                         const StepParams<real> P, int band) {
     __shared__ real s_psi[4][TX + 2];
     const int nx = P.nx, ny = P.ny;
     const long long pitch = P.pitch;
     const int x0 = blockIdx.x * TX;
     const int w = min(TX, nx - x0);
-    const int y0 = blockIdx.y * P.rows;
-    const int y1 = min(y0 + P.rows, ny);
+    const int y0 = band > 0 ? (blockIdx.y == 0 ? 0 : ny - band) : blockIdx.y * P.rows;
+    const int y1 = band > 0 ? y0 + band : min(y0 + P.rows, ny);
     const int t = threadIdx.x;
     const bool is_main = t < TX;
     bool has_col;
@@ -174,15 +182,15 @@ __global__ void __launch_bounds__(TX + 32) pp_step_walls(const real* __restrict_
 // rho (8 rows, 2 halo columns each side), mu (4 rows, 1 halo column).
 template <typename real, int TX>
 __global__ void __launch_bounds__(TX + 32) fe_step_walls(const real* __restrict__ fin, real* __restrict__ fout,
-                                                         const StepParams<real> P) {
+                                                         const StepParams<real> P, int band) {
     __shared__ real s_rho[8][TX + 4];
     __shared__ real s_mu[4][TX + 2];
     const int nx = P.nx, ny = P.ny;
     const long long pitch = P.pitch;
     const int x0 = blockIdx.x * TX;
     const int w = min(TX, nx - x0);
-    const int y0 = blockIdx.y * P.rows;
-    const int y1 = min(y0 + P.rows, ny);
+    const int y0 = band > 0 ? (blockIdx.y == 0 ? 0 : ny - band) : blockIdx.y * P.rows;
+    const int y1 = band > 0 ? y0 + band : min(y0 + P.rows, ny);
     const int t = threadIdx.x;
     const bool is_main = t < TX;
     bool has_col, has_mu;
