@@ -49,6 +49,8 @@ class Params(ctypes.Structure):
         ("sigma_Li", ctypes.c_double), ("kappa", ctypes.c_double),
         ("fx", ctypes.c_double), ("fy", ctypes.c_double),
         ("walls", ctypes.c_double),
+        ("drive", ctypes.c_double), ("drive_ax_lo", ctypes.c_double),
+        ("drive_ax_hi", ctypes.c_double), ("drive_x_split", ctypes.c_double),
     ]
 
 
@@ -56,7 +58,8 @@ def make_params(**kw) -> Params:
     """Build oracle parameters; unspecified relaxation times default to 1, G to -1."""
     d = dict(a=0.5, b=4.0, R=1.0, T=0.0, G=-1.0, tau_rho=1.0, tau_e=1.0, tau_zeta=1.0,
              tau_j=1.0, tau_q=1.0, tau_nu=1.0, kappa_P=1.0, kappa_Li=0.0, sigma_Li=0.0,
-             kappa=0.5, fx=0.0, fy=0.0, walls=0.0)
+             kappa=0.5, fx=0.0, fy=0.0, walls=0.0, drive=0.0, drive_ax_lo=0.0, drive_ax_hi=0.0,
+             drive_x_split=0.0)
     unknown = set(kw) - set(d)
     if unknown:
         raise KeyError(f"unknown oracle parameter(s): {sorted(unknown)}")
@@ -128,6 +131,23 @@ def run(model: int, p: Params, f: np.ndarray, nsteps: int, nthreads: int = 0) ->
     done = lib().orc_run(model, ctypes.byref(p), nx, ny, _ptr(f), int(nsteps), int(nthreads))
     if done != nsteps:
         raise FloatingPointError(f"oracle state became invalid after {done} of {nsteps} steps")
+    return f
+
+
+def run_driven(model: int, p: Params, f: np.ndarray, nsteps: int, t0: int, t_on: int) -> np.ndarray:
+    """Advance a state at time t0 by nsteps with the droplet-collision force of Sec. 5.4 (the
+    drive_* fields of p) acting on the collisions of states at times t > t_on only."""
+    import copy
+
+    off = copy.copy(p)
+    off.drive = 0.0
+    on = copy.copy(p)
+    on.drive = 1.0
+    n_off = max(0, min(nsteps, t_on + 1 - t0))
+    if n_off:
+        f = run(model, off, f, n_off)
+    if nsteps - n_off:
+        f = run(model, on, f, nsteps - n_off)
     return f
 
 

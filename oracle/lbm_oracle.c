@@ -67,6 +67,8 @@ typedef struct {
     double kappa;       /* FE-LBM surface-tension parameter, mu = mu_b - kappa lap rho */
     double fx, fy;      /* constant body force added to the total force */
     double walls;       /* 0: periodic in y; 1: no-slip walls on rows 0 and ny-1 (Sec. 5.3) */
+    double drive;       /* 1: add the droplet-collision force of Sec. 5.4 (drive_force) */
+    double drive_ax_lo, drive_ax_hi, drive_x_split;
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -288,6 +290,21 @@ static void wall_fill(const orc_params* p, int nx, int ny, double* f, const doub
     }
 }
 
+/* Sec. 5.4: the horizontal force a_x |rho - rho_ave| that drives two droplets together;
+ * a_x = drive_ax_lo for x <= drive_x_split and drive_ax_hi beyond, rho_ave the mean density
+ * of the domain (domain_mean, taken every step).  It is an external force: it enters the
+ * total force but not the interaction force of the sigma^Li term. */
+static double domain_mean(const double* rho, size_t N) {
+    double s = 0.0;
+    for (size_t c = 0; c < N; ++c) s += rho[c];
+    return s / (double)N;
+}
+static double drive_force(const orc_params* p, int x, double rho, double rho_ave) {
+    if (p->drive == 0.0) return 0.0;
+    const double ax = (double)x <= p->drive_x_split ? p->drive_ax_lo : p->drive_ax_hi;
+    return ax * fabs(rho - rho_ave);
+}
+
 static inline int is_wall_row(const orc_params* p, int y, int ny) {
     return p->walls != 0.0 && (y == 0 || y == ny - 1);
 }
@@ -308,13 +325,14 @@ static int pp_fields(const orc_params* p, int nx, int ny, double* f, double* rho
         if (psi[c] < 0.0 || !(s > 0.0)) bad = 1;
     }
     if (bad) return -1;
+    const double rave = p->drive != 0.0 ? domain_mean(rho, N) : 0.0;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t c = (size_t)y * nx + x;
             double fix, fiy;
             sc_force(p, psi, nx, ny, x, y, &fix, &fiy);
-            Fx[c] = fix + p->fx;
+            Fx[c] = fix + p->fx + drive_force(p, x, rho[c], rave);
             Fy[c] = is_wall_row(p, y, ny) ? p->fy : fiy + p->fy;
         }
     if (p->walls != 0.0) wall_fill(p, nx, ny, f, Fx);
@@ -340,6 +358,7 @@ static int pp_step(const orc_params* p, int nx, int ny, double* f, double* fnew,
                    double* rho, double* psi, double* Fx, double* Fy, double* ux, double* uy) {
     size_t N = (size_t)nx * ny;
     if (pp_fields(p, nx, ny, f, rho, psi, Fx, Fy, ux, uy)) return -1;
+    const double rave = p->drive != 0.0 ? domain_mean(rho, N) : 0.0;
     double L[Q9];
     lambda_diag(p, L);
 #pragma omp parallel for schedule(static)
@@ -359,7 +378,7 @@ static int pp_step(const orc_params* p, int nx, int ny, double* f, double* fnew,
             }
             /* Eq. (32): forcing in moment space.  The consistency term uses only the
              * interaction force F_int; the velocity terms use the total force. */
-            double fix = Fx[c] - p->fx, fiy = Fy[c] - p->fy;
+            double fix = Fx[c] - p->fx - drive_force(p, x, rho[c], rave), fiy = Fy[c] - p->fy;
             double Fint2 = fix * fix + fiy * fiy;
             double uF = ux[c] * Fx[c] + uy[c] * Fy[c];
             double ps2 = psi[c] * psi[c];
@@ -431,6 +450,7 @@ static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho
         if (!(s > 0.0) || !(p->b * s / 4.0 < 1.0)) bad = 1;
     }
     if (bad) return -1;
+    const double rave = p->drive != 0.0 ? domain_mean(rho, N) : 0.0;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
@@ -444,7 +464,7 @@ static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho
             double gmx, gmy;
             stencil_grad(mu, nx, ny, p->walls != 0.0, x, y, &gmx, &gmy);
             stencil_grad(rho, nx, ny, p->walls != 0.0, x, y, &drx[c], &dry[c]);
-            Fx[c] = -rho[c] * gmx + p->fx;
+            Fx[c] = -rho[c] * gmx + p->fx + drive_force(p, x, rho[c], rave);
             Fy[c] = -rho[c] * gmy + p->fy;
             if (is_wall_row(p, y, ny)) {  /* mirrored neighbours: no normal gradient */
                 Fy[c] = p->fy;
