@@ -250,7 +250,10 @@ def run_walls(args, peak):
     both models (periodic strip kernel on the whole lattice, then the wall bands recomputed by
     the wall kernel; two launches per step) on a size x size plate channel (vapour below, liquid above, sine-perturbed
     interface, F_x = 1e-6), CUDA events around 500 steps on the launching stream; and the
-    wall-clock rate of the 101 x 50 FP64 channel of Sec. 5.3 (steps/s over 2e4 steps)."""
+    wall-clock rate of the 101 x 50 FP64 channel of Sec. 5.3 (steps/s over 2e4 steps); and the
+    droplet-collision drive of Sec. 5.4 (a domain-mean reduction plus a direct step per step):
+    steps/s of the 200 x 100 FP64 pair, and FP32 throughput of a size x size pair (the extra
+    read of the reduction is not counted in the 72 B/cell of the fraction)."""
     import numpy as np
     import torch
 
@@ -277,8 +280,8 @@ def run_walls(args, peak):
             gbs = BYTES_PER_CELL_F32 * size * size / s / 1e9
             out[key] = {"mlups": size * size / s / 1e6, "us_per_launch": s * 1e6, "gbs_at_72B": gbs,
                         "frac_of_hbm": gbs / peak,
-                        "kernels": ("pp_step_pair + pp_step_walls (wall bands, 2 rows)",
-                                    "fe_step_pair + fe_step_walls (wall bands, 3 rows)")[model]}
+                        "kernels": ("pp_step_pair + pp_step_ext (wall bands, 2 rows)",
+                                    "fe_step_pair + fe_step_ext (wall bands, 3 rows)")[model]}
             ctx.close()
         rates = {}
         for model, key in ((0, "pseudopotential"), (1, "free_energy")):
@@ -296,6 +299,33 @@ def run_walls(args, peak):
             rates[key] = 20000 / (time.perf_counter() - t)
             ctx.close()
         out["sec53_channel_f64_steps_per_s"] = rates
+        # Sec. 5.4: droplet pair driven together (domain-mean reduction + direct step per step)
+        col = {}
+        for model, key in ((0, "pseudopotential"), (1, "free_energy")):
+            kw = dict(a=0.25, Tr=0.8, tau_nu=1.0)
+            kw.update({"match_kappa": 0.5, "tau_e": 1.0} if model == 0 else {"tau_e": 0.75, "kappa": 0.5})
+            for prec, pk in ((lbm.LBM_F64, "f64_200x100_steps_per_s"), (lbm.LBM_F32, "f32_4096_mlups")):
+                nx, ny = (200, 100) if prec == lbm.LBM_F64 else (size, size)
+                p = lbm.lbm_params_default(model, precision=prec, **kw)
+                ctx = lbm.Context(p, nx, ny, stream=stream)
+                _, th = ctx.derived()
+                ctx.set_density(inputs.two_droplets(nx, ny, [(nx / 4, ny / 2), (3 * nx / 4, ny / 2)], ny / 4,
+                                                    th.rho_v, th.rho_l))
+                ctx.set_drive(5e-6, -5e-6, nx // 2, 0)
+                ctx.step(128)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                n = 20000 if prec == lbm.LBM_F64 else 256
+                torch.cuda.synchronize()
+                e0.record(stream)
+                ctx.step(n)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) * 1e-3
+                col.setdefault(key, {})[pk] = n / sec if prec == lbm.LBM_F64 else nx * ny * n / sec / 1e6
+                if prec == lbm.LBM_F32:
+                    col[key]["f32_4096_frac_of_hbm_at_72B"] = BYTES_PER_CELL_F32 * nx * ny * n / sec / 1e9 / peak
+                ctx.close()
+        out["collision_sec54"] = col
     return out
 
 

@@ -160,6 +160,17 @@ int lbm_set_density_device(lbm_ctx* ctx, const void* rho0_device);
 int lbm_set_populations(lbm_ctx* ctx, const double* f);
 int lbm_get_populations(lbm_ctx* ctx, double* f);
 
+/* Droplet-collision drive of Sec. 5.4: from now on the collision of every state at time
+ * t > t_on (t = steps taken since lbm_set_density) adds to the x force of each cell
+ *   F_x += a_x |rho - rho_ave|,  a_x = ax_lo where x <= x_split, ax_hi where x > x_split,
+ * rho_ave the mean density of that state (reduced on the device every step).  The force is
+ * external: it enters the total force (velocity, forcing moments) but not the interaction
+ * force of the sigma^Li term (Eq. 32).  Sec. 5.4 uses ax_lo = 5e-6, ax_hi = -5e-6,
+ * x_split = 100, t_on = 2000 on a 200 x 100 lattice.  Steps with the drive run the direct
+ * kernels.  Errors: LBM_ERR_ARG for a non-finite value, LBM_ERR_UNSUPPORTED with walls (the
+ * reduction sums the stored populations of a periodic lattice).  Synchronises the stream. */
+int lbm_set_drive(lbm_ctx* ctx, double ax_lo, double ax_hi, double x_split, long long t_on);
+
 /* Advance nsteps time steps (Eq. 1: collision and streaming).  Asynchronous: kernels
  * are enqueued (CUDA-graph replays of 64-step chunks plus single launches) and the
  * call returns.  Returns LBM_ERR_DIVERGED if a previous observables call saw a

@@ -18,7 +18,7 @@
 #include "step_tma.cuh"
 #include "step_warp.cuh"
 #include "step_pair.cuh"
-#include "step_walls.cuh"
+#include "step_ext.cuh"
 #include "thermo.h"
 
 namespace {
@@ -106,10 +106,13 @@ struct lbm_ctx {
     int* d_err;          // device error word of the TMA kernels (bounded waits)
     bool use_tma;
     bool walls;          // no-slip walls on rows 0 and ny-1 (direct wall kernels)
+    bool drive;          // droplet-collision drive configured (lbm_set_drive)
+    double drive_lo, drive_hi, drive_split;
+    long long drive_t_on;
     double* h_pinned;    // 8 doubles, pinned
     cudaStream_t stream;
     bool own_stream;
-    cudaGraphExec_t graph[2];
+    cudaGraphExec_t graph[2][2];  // [buffer parity][drive active]
     long long step;
     int status;
     bool ready;
@@ -449,7 +452,8 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
         }
         c->own_stream = true;
     }
-    c->graph[0] = c->graph[1] = nullptr;
+    c->graph[0][0] = c->graph[0][1] = c->graph[1][0] = c->graph[1][1] = nullptr;
+    c->drive = false;
     c->cur = 0;
     c->step = 0;
     c->status = LBM_OK;
@@ -488,7 +492,8 @@ extern "C" void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 2; ++i)
-        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+        for (int m = 0; m < 2; ++m)
+            if (c->graph[i][m]) cudaGraphExecDestroy(c->graph[i][m]);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->own_ws) cudaFree(c->ws);
@@ -507,7 +512,62 @@ extern "C" int lbm_derived(const lbm_ctx* c, lbm_params* resolved, lbm_thermo* t
 // ----------------------------------------------------------------------------
 // Kernel launches
 
-static int launch_step(lbm_ctx* c, int src) {
+constexpr int kMassBlocks = 608;  // block sums of the drive's domain mean (4 x 152 SMs; < 3 kRedBlocks)
+
+template <typename real>
+static lbmk::Drive<real> no_drive() {
+    lbmk::Drive<real> d{};
+    d.rho_ave = nullptr;
+    return d;
+}
+
+// The drive of the state in buffer src: its mean density reduced on the context stream into
+// partials[kMassBlocks] (block sums in partials[0, kMassBlocks)).
+template <typename real>
+static lbmk::Drive<real> launch_drive(lbm_ctx* c, int src) {
+    const long long n = (long long)c->nx * c->ny;
+    lbmk::mass_partials_kernel<real><<<kMassBlocks, 256, 0, c->stream>>>(static_cast<const real*>(c->f[src]),
+                                                                       c->pitch, n, c->partials);
+    lbmk::mass_final_kernel<<<1, 32, 0, c->stream>>>(c->partials, kMassBlocks, 1.0 / (double)n,
+                                                     c->partials + kMassBlocks);
+    lbmk::Drive<real> d;
+    d.rho_ave = c->partials + kMassBlocks;
+    d.x_split = (int)std::floor(std::min(std::max(c->drive_split, -1.0), (double)c->nx));
+    d.ax_lo = (real)c->drive_lo;
+    d.ax_hi = (real)c->drive_hi;
+    return d;
+}
+
+// One step with the droplet-collision drive acting (periodic lattice, direct kernels).
+static int launch_step_driven(lbm_ctx* c, int src) {
+    const void* fin = c->f[src];
+    void* fout = c->f[src ^ 1];
+    const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
+    if (c->prec == LBM_F32) {
+        const lbmk::Drive<float> d = launch_drive<float>(c, src);
+        dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
+        if (pp)
+            lbmk::pp_step_ext<float, kTXf, false>
+                <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, d);
+        else
+            lbmk::fe_step_ext<float, kTXf, false>
+                <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, d);
+    } else {
+        const lbmk::Drive<double> d = launch_drive<double>(c, src);
+        dim3 grid((c->nx + kTXd - 1) / kTXd, (c->ny + c->rows - 1) / c->rows);
+        if (pp)
+            lbmk::pp_step_ext<double, kTXd, false>
+                <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, d);
+        else
+            lbmk::fe_step_ext<double, kTXd, false>
+                <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, d);
+    }
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+static int launch_step(lbm_ctx* c, int src, bool driven = false) {
+    if (driven) return launch_step_driven(c, src);
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
@@ -518,30 +578,32 @@ static int launch_step(lbm_ctx* c, int src) {
             dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
             lbmk::pp_step_pair<kPPPWarps, kPPPStages><<<grid, (kPPPWarps + 1) * 32, sizeof(PPPSmem), c->stream>>>(
                 (const float*)fin, (float*)fout, c->spf, c->d_err);
-            lbmk::pp_step_walls<float, kTXf><<<dim3((c->nx + kTXf - 1) / kTXf, 2), kTXf + 32, 0, c->stream>>>(
-                (const float*)fin, (float*)fout, c->spf, band);
+            lbmk::pp_step_ext<float, kTXf, true><<<dim3((c->nx + kTXf - 1) / kTXf, 2), kTXf + 32, 0, c->stream>>>(
+                (const float*)fin, (float*)fout, c->spf, band, no_drive<float>());
         } else {
             dim3 grid((c->nx + kFEPTX - 1) / kFEPTX, (c->ny + c->rows - 1) / c->rows);
             lbmk::fe_step_pair<kFEPWarps, kFEPStages><<<grid, (kFEPWarps + 1) * 32, sizeof(FEPSmem), c->stream>>>(
                 (const float*)fin, (float*)fout, c->spf, c->d_err);
-            lbmk::fe_step_walls<float, kTXf><<<dim3((c->nx + kTXf - 1) / kTXf, 2), kTXf + 32, 0, c->stream>>>(
-                (const float*)fin, (float*)fout, c->spf, band);
+            lbmk::fe_step_ext<float, kTXf, true><<<dim3((c->nx + kTXf - 1) / kTXf, 2), kTXf + 32, 0, c->stream>>>(
+                (const float*)fin, (float*)fout, c->spf, band, no_drive<float>());
         }
     } else if (c->walls) {
         if (c->prec == LBM_F32) {
             dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
             if (pp)
-                lbmk::pp_step_walls<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0);
+                lbmk::pp_step_ext<float, kTXf, true>
+                    <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, no_drive<float>());
             else
-                lbmk::fe_step_walls<float, kTXf><<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0);
+                lbmk::fe_step_ext<float, kTXf, true>
+                    <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, no_drive<float>());
         } else {
             dim3 grid((c->nx + kTXd - 1) / kTXd, (c->ny + c->rows - 1) / c->rows);
             if (pp)
-                lbmk::pp_step_walls<double, kTXd>
-                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0);
+                lbmk::pp_step_ext<double, kTXd, true>
+                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, no_drive<double>());
             else
-                lbmk::fe_step_walls<double, kTXd>
-                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0);
+                lbmk::fe_step_ext<double, kTXd, true>
+                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, no_drive<double>());
         }
     } else if (c->use_tma && pp && kPPPair) {
         dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
@@ -582,13 +644,13 @@ static int launch_step(lbm_ctx* c, int src) {
     return LBM_OK;
 }
 
-static int build_graph(lbm_ctx* c, int parity) {
+static int build_graph(lbm_ctx* c, int parity, int driven) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = LBM_OK;
     int src = parity;
     for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) {
-        rc = launch_step(c, src);
+        rc = launch_step(c, src, driven != 0);
         src ^= 1;
     }
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
@@ -597,33 +659,58 @@ static int build_graph(lbm_ctx* c, int parity) {
         return rc;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    e = cudaGraphInstantiate(&c->graph[parity][driven], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     return LBM_OK;
 }
+
+// Whether the collision of the state at time t is driven (Sec. 5.4: after t_on).
+static bool driven_at(const lbm_ctx* c, long long t) { return c->drive && t > c->drive_t_on; }
 
 extern "C" int lbm_step(lbm_ctx* c, long long nsteps) {
     if (!c || nsteps < 0) return LBM_ERR_ARG;
     if (!c->ready) return LBM_ERR_STATE;
     if (c->status) return c->status;
     while (nsteps > 0) {
-        if (nsteps >= kGraphSteps) {
-            if (!c->graph[c->cur]) {
-                int rc = build_graph(c, c->cur);
+        const bool driven = driven_at(c, c->step);
+        // a 64-step graph replays one kind of step: the chunk must not straddle t_on
+        const bool uniform = driven_at(c, c->step + kGraphSteps - 1) == driven;
+        if (nsteps >= kGraphSteps && uniform) {
+            cudaGraphExec_t& gx = c->graph[c->cur][driven ? 1 : 0];
+            if (!gx) {
+                int rc = build_graph(c, c->cur, driven ? 1 : 0);
                 if (rc) return rc;
             }
-            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+            CK(cudaGraphLaunch(gx, c->stream));
             nsteps -= kGraphSteps;
             c->step += kGraphSteps;  // even count: buffer parity unchanged
         } else {
-            int rc = launch_step(c, c->cur);
+            int rc = launch_step(c, c->cur, driven);
             if (rc) return rc;
             c->cur ^= 1;
             --nsteps;
             ++c->step;
         }
     }
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_drive(lbm_ctx* c, double ax_lo, double ax_hi, double x_split, long long t_on) {
+    if (!c || !std::isfinite(ax_lo) || !std::isfinite(ax_hi) || !std::isfinite(x_split)) return LBM_ERR_ARG;
+    if (c->walls) return LBM_ERR_UNSUPPORTED;
+    c->drive = true;
+    c->drive_lo = ax_lo;
+    c->drive_hi = ax_hi;
+    c->drive_split = x_split;
+    c->drive_t_on = t_on;
+    // captured driven steps hold the old constants
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 2; ++i)
+        if (c->graph[i][1]) {
+            cudaGraphExecDestroy(c->graph[i][1]);
+            c->graph[i][1] = nullptr;
+        }
     return LBM_OK;
 }
 
@@ -767,12 +854,20 @@ static int compute_fields(lbm_ctx* c, const lbmk::StepParams<real>& sp) {
     real* uy = ux + n;
     const real* f = static_cast<const real*>(c->f[c->cur]);
     const int model = c->prm.model;
-    if (c->walls) {
+    if (c->walls || driven_at(c, c->step)) {
         real* fw = static_cast<real*>(c->f[c->cur]);
-        lbmk::rho_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, sp, model);
-        if (model == LBM_FREE_ENERGY) lbmk::mu_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
-        lbmk::walls_complete_kernel<real><<<(2 * c->nx + 255) / 256, 256, 0, c->stream>>>(fw, rho, aux, sp, model);
-        lbmk::velocity_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, ux, uy, sp, model);
+        if (c->walls) {
+            lbmk::rho_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, sp, model);
+            if (model == LBM_FREE_ENERGY) lbmk::mu_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
+            lbmk::walls_complete_kernel<real>
+                <<<(2 * c->nx + 255) / 256, 256, 0, c->stream>>>(fw, rho, aux, sp, model);
+        } else {
+            lbmk::rho_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(f, rho, aux, sp, model);
+            if (model == LBM_FREE_ENERGY) lbmk::mu_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
+        }
+        const lbmk::Drive<real> d = driven_at(c, c->step) ? launch_drive<real>(c, c->cur) : no_drive<real>();
+        lbmk::velocity_ext_kernel<real>
+            <<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, ux, uy, sp, model, c->walls ? 1 : 0, d);
         CK(cudaGetLastError());
         return LBM_OK;
     }

@@ -1,6 +1,7 @@
-// step_walls.cuh -- the time step and the field kernels of a channel bounded by no-slip
-// walls on rows 0 and ny-1 (periodic in x): the two-phase flow between parallel plates of
-// Sec. 5.3, driven by the constant body force of StepParams::fx, fy.
+// step_ext.cuh -- direct step and field kernels with the two extensions of the paper's flow
+// tests: no-slip walls on rows 0 and ny-1 (periodic in x; the two-phase flow between
+// parallel plates of Sec. 5.3, driven by the constant body force of StepParams::fx, fy) and
+// the density-dependent drive of the droplet collision of Sec. 5.4 (Drive).
 //
 // Wall treatment (Zou and He's velocity condition, cited in Sec. 5.3):
 //   * a wall node lacks the populations that would stream in from beyond the wall (bottom:
@@ -16,10 +17,18 @@
 //     holds S_i(y) = f_i(y + c_i)) their slots are exactly the slots a wall node pulls its
 //     unknowns from, which the fill overwrites.
 //
+// Droplet-collision drive (Sec. 5.4): the force a_x |rho - rho_ave| along x, a_x = ax_lo for
+// x <= x_split and ax_hi beyond, rho_ave the mean density of the state being collided, from
+// block sums of every stored population (mass_partials_kernel and mass_final_kernel, launched
+// before the step: the pull layout holds each population of a periodic lattice exactly once).  It is an external
+// force: it adds to the total force like the body force and stays out of the interaction
+// force of Eq. (32)'s sigma^Li term.
+//
 // The kernels follow the direct step kernels of lbm_kernels.cuh (one column per thread,
-// shared-memory rings of the neighbour fields, one halo warp); the pulled rows map through
-// mirror_row, wall rows get the two fills, and a wall row's collision sees its neighbour
-// fields mirrored.  Requirements (checked on the host): ny >= 4.
+// shared-memory rings of the neighbour fields, one halo warp).  With WALLS the pulled rows
+// map through mirror_row, wall rows get the two fills, and a wall row's collision sees its
+// neighbour fields mirrored; without, rows wrap.  Requirements (checked on the host): with
+// walls ny >= 4.
 //
 // band > 0 launches only the rows next to the walls: grid.y = 2, CTA row 0 updates rows
 // [0, band), CTA row 1 rows [ny - band, ny).  This completes a step whose interior was
@@ -81,25 +90,92 @@ __device__ __forceinline__ real grad_x(const real n[9]) {
     return (n[1] - n[3]) * real(1.0 / 3.0) + ((n[5] - n[7]) + (n[8] - n[6])) * real(1.0 / 12.0);
 }
 
-// Pulled populations of row y (already mirrored) of column x; a wall row gets the first
-// fill, J = (0, -fy/2).  The pull of a wall row reads its unknowns from the wrapped row:
-// in bounds, and overwritten by the fill.
-template <typename real>
-__device__ __forceinline__ void pull_row_walls(const real* __restrict__ f, const StepParams<real>& P, int x, int xm,
-                                               int xp, int y, real v[9]) {
+// Row seen by a stencil: mirrored through a wall, or wrapped (periodic; any ny >= 1).
+template <bool WALLS>
+__device__ __forceinline__ int stencil_row(int y, int ny) {
+    return WALLS ? mirror_row(y, ny) : ((y % ny) + ny) % ny;
+}
+
+// Pulled populations of row y (already mapped) of column x; with walls a wall row gets the
+// first fill, J = (0, -fy/2).  The pull of a wall row reads its unknowns from the wrapped
+// row: in bounds, and overwritten by the fill.
+template <bool WALLS, typename real>
+__device__ __forceinline__ void pull_row_ext(const real* __restrict__ f, const StepParams<real>& P, int x, int xm,
+                                             int xp, int y, real v[9]) {
     const int ny = P.ny, nx = P.nx;
     const long long om = (long long)(y == 0 ? ny - 1 : y - 1) * nx, o0 = (long long)y * nx,
                     op = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
     pull9(f, P.pitch, x, xm, xp, om, o0, op, v);
-    if (y == 0 || y == ny - 1) wall_fill(v, y != 0, real(0), real(-0.5) * P.fy);
+    if (WALLS && (y == 0 || y == ny - 1)) wall_fill(v, y != 0, real(0), real(-0.5) * P.fy);
+}
+
+// Droplet-collision drive; rho_ave == nullptr: none.
+template <typename real>
+struct Drive {
+    const double* rho_ave;  // mean density of the state being collided (device scalar)
+    int x_split;
+    real ax_lo, ax_hi;
+};
+
+// Parameters of one cell's collision with the drive added to the body force.
+template <typename real>
+__device__ __forceinline__ StepParams<real> with_drive(const StepParams<real>& P, const Drive<real>& D, int x,
+                                                       real rho, real rho_ave) {
+    StepParams<real> Q = P;
+    const real d = rho > rho_ave ? rho - rho_ave : rho_ave - rho;
+    Q.fx = P.fx + (x <= D.x_split ? D.ax_lo : D.ax_hi) * d;
+    return Q;
+}
+
+// Block sums of every stored population (9 planes of n cells) into out[blockIdx.x]: per thread
+// a plane-by-plane strided sum (in the storage precision within a plane, FP64 across planes and
+// in the block tree).  Fixed grid and order: deterministic.
+template <typename real>
+__global__ void __launch_bounds__(256) mass_partials_kernel(const real* __restrict__ f, long long pitch, long long n,
+                                                            double* __restrict__ out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double s = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < 9; ++i) {
+        const real* p = f + i * pitch;
+        real a = real(0), b = real(0);
+        long long k = t0;
+        for (; k + stride < n; k += 2 * stride) {
+            a += __ldg(p + k);
+            b += __ldg(p + k + stride);
+        }
+        if (k < n) a += __ldg(p + k);
+        s += (double)a + (double)b;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double ws[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) ws[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        out[blockIdx.x] = t;
+    }
+}
+
+// rho_ave = (sum of nparts block sums) * inv_cells into *rho_ave; one warp, fixed order.
+__global__ void mass_final_kernel(const double* __restrict__ parts, int nparts, double inv_cells,
+                                  double* __restrict__ rho_ave) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += 32) s += parts[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *rho_ave = s * inv_cells;
 }
 
 // ---------------------------------------------------------------------------------
-// Pseudopotential step between walls (Eqs. 1, 4, 6, 10, 11, 13, 30-32).
-template <typename real, int TX>
-__global__ void __launch_bounds__(TX + 32) pp_step_walls(const real* __restrict__ fin, real* __restrict__ fout,
-                                                         const StepParams<real> P, int band) {
+// Pseudopotential step (Eqs. 1, 4, 6, 10, 11, 13, 30-32) with walls and/or the drive.
+template <typename real, int TX, bool WALLS>
+__global__ void __launch_bounds__(TX + 32) pp_step_ext(const real* __restrict__ fin, real* __restrict__ fout,
+                                                       const StepParams<real> P, int band, const Drive<real> D) {
     __shared__ real s_psi[4][TX + 2];
+    const real s_rave = D.rho_ave ? real(*D.rho_ave) : real(0);
     const int nx = P.nx, ny = P.ny;
     const long long pitch = P.pitch;
     const int x0 = blockIdx.x * TX;
@@ -126,7 +202,7 @@ __global__ void __launch_bounds__(TX + 32) pp_step_walls(const real* __restrict_
     real cur[9], prv[9];
     real rho_cur = real(1), rho_prv = real(1);
     if (has_col) {
-        pull_row_walls(fin, P, x, xm, xp, mirror_row(y0 - 1, ny), cur);
+        pull_row_ext<WALLS>(fin, P, x, xm, xp, stencil_row<WALLS>(y0 - 1, ny), cur);
         rho_cur = sum9(cur);
     }
 #pragma unroll 1
@@ -134,7 +210,7 @@ __global__ void __launch_bounds__(TX + 32) pp_step_walls(const real* __restrict_
         real nxt[9];
         real rho_nxt = real(1);
         if (has_col && r < y1) {
-            pull_row_walls(fin, P, x, xm, xp, mirror_row(r + 1, ny), nxt);
+            pull_row_ext<WALLS>(fin, P, x, xm, xp, stencil_row<WALLS>(r + 1, ny), nxt);
             rho_nxt = sum9(nxt);
         }
         if (has_col) s_psi[r & 3][sc] = pseudo_psi(rho_cur, P);
@@ -155,12 +231,15 @@ __global__ void __launch_bounds__(TX + 32) pp_step_walls(const real* __restrict_
             pn[6] = sp[sc - 1];
             pn[7] = sm[sc - 1];
             pn[8] = sm[sc + 1];
-            if (c == 0 || c == ny - 1) {
+            if (WALLS && (c == 0 || c == ny - 1)) {
                 mirror_neighbours(pn, c != 0);
                 const real Fx = pn[0] * grad_x(pn) + P.fx;  // F_int,x + body force (Eq. 10)
                 wall_fill(prv, c != 0, real(-0.5) * Fx, real(-0.5) * P.fy);
             }
-            pp_collide(prv, rho_prv, pn[0], pn, P);
+            if (D.rho_ave)
+                pp_collide(prv, rho_prv, pn[0], pn, with_drive(P, D, x, rho_prv, s_rave));
+            else
+                pp_collide(prv, rho_prv, pn[0], pn, P);
             const long long o = (long long)c * nx + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = prv[i];
@@ -178,13 +257,14 @@ __global__ void __launch_bounds__(TX + 32) pp_step_walls(const real* __restrict_
 }
 
 // ---------------------------------------------------------------------------------
-// Free-energy step between walls (Eqs. 1, 6, 20, 21, 24, 29).  Rings as in fe_step_kernel:
+// Free-energy step (Eqs. 1, 6, 20, 21, 24, 29) with walls and/or the drive.  Rings as in fe_step_kernel:
 // rho (8 rows, 2 halo columns each side), mu (4 rows, 1 halo column).
-template <typename real, int TX>
-__global__ void __launch_bounds__(TX + 32) fe_step_walls(const real* __restrict__ fin, real* __restrict__ fout,
-                                                         const StepParams<real> P, int band) {
+template <typename real, int TX, bool WALLS>
+__global__ void __launch_bounds__(TX + 32) fe_step_ext(const real* __restrict__ fin, real* __restrict__ fout,
+                                                       const StepParams<real> P, int band, const Drive<real> D) {
     __shared__ real s_rho[8][TX + 4];
     __shared__ real s_mu[4][TX + 2];
+    const real s_rave = D.rho_ave ? real(*D.rho_ave) : real(0);
     const int nx = P.nx, ny = P.ny;
     const long long pitch = P.pitch;
     const int x0 = blockIdx.x * TX;
@@ -213,11 +293,11 @@ __global__ void __launch_bounds__(TX + 32) fe_step_walls(const real* __restrict_
     const int xm = x == 0 ? nx - 1 : x - 1;
     const int xp = x == nx - 1 ? 0 : x + 1;
     real p0[9], p1[9], p2[9];  // pulled populations of rows r-2, r-1, r
-    if (has_col) pull_row_walls(fin, P, x, xm, xp, mirror_row(y0 - 2, ny), p2);
+    if (has_col) pull_row_ext<WALLS>(fin, P, x, xm, xp, stencil_row<WALLS>(y0 - 2, ny), p2);
 #pragma unroll 1
     for (int r = y0 - 2; r <= y1 + 1; ++r) {
         real nxt[9];
-        if (has_col && r <= y1) pull_row_walls(fin, P, x, xm, xp, mirror_row(r + 1, ny), nxt);
+        if (has_col && r <= y1) pull_row_ext<WALLS>(fin, P, x, xm, xp, stencil_row<WALLS>(r + 1, ny), nxt);
         if (has_col) s_rho[r & 7][rc] = sum9(p2);
         __syncthreads();
         if (has_mu && r >= y0) {
@@ -252,7 +332,7 @@ __global__ void __launch_bounds__(TX + 32) fe_step_walls(const real* __restrict_
             rn[1] = r0[rc + 1]; rn[2] = rp[rc]; rn[3] = r0[rc - 1]; rn[4] = rm[rc];
             rn[5] = rp[rc + 1]; rn[6] = rp[rc - 1]; rn[7] = rm[rc - 1]; rn[8] = rm[rc + 1];
             const real rho_c = r0[rc];
-            if (c == 0 || c == ny - 1) {
+            if (WALLS && (c == 0 || c == ny - 1)) {
                 // mu beyond the wall is mu of the mirrored row (the ring holds the value
                 // recomputed from mirrored rho, equal up to rounding order)
                 mirror_neighbours(mn, c != 0);
@@ -260,7 +340,10 @@ __global__ void __launch_bounds__(TX + 32) fe_step_walls(const real* __restrict_
                 const real Fx = -rho_c * grad_x(mn) + P.fx;  // F = -rho grad mu + body force
                 wall_fill(p0, c != 0, real(-0.5) * Fx, real(-0.5) * P.fy);
             }
-            fe_collide(p0, rho_c, mn, rn, P);
+            if (D.rho_ave)
+                fe_collide(p0, rho_c, mn, rn, with_drive(P, D, x, rho_c, s_rave));
+            else
+                fe_collide(p0, rho_c, mn, rn, P);
             const long long o = (long long)c * nx + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
@@ -279,12 +362,14 @@ __global__ void __launch_bounds__(TX + 32) fe_step_walls(const real* __restrict_
 // ---------------------------------------------------------------------------------
 // Fields of the current state of a walled channel (observables, not on the step path).
 
-// Values at x + c_i with rows beyond a wall mirrored; n[0] is the cell itself.
+// Values at x + c_i with rows beyond a wall mirrored (walls) or wrapped; n[0] is the cell.
 template <typename real>
-__device__ __forceinline__ void gather8_walls(const real* __restrict__ a, int x, int y, int nx, int ny, real n[9]) {
+__device__ __forceinline__ void gather8_ext(const real* __restrict__ a, int x, int y, int nx, int ny, bool walls,
+                                            real n[9]) {
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const long long ym = (long long)mirror_row(y - 1, ny) * nx, y0 = (long long)y * nx,
-                    yp = (long long)mirror_row(y + 1, ny) * nx;
+    const int rm = walls ? mirror_row(y - 1, ny) : (y == 0 ? ny - 1 : y - 1);
+    const int rp = walls ? mirror_row(y + 1, ny) : (y == ny - 1 ? 0 : y + 1);
+    const long long ym = (long long)rm * nx, y0 = (long long)y * nx, yp = (long long)rp * nx;
     n[0] = a[y0 + x];
     n[1] = a[y0 + xp];
     n[2] = a[yp + x];
@@ -304,7 +389,7 @@ __global__ void rho_walls_kernel(const real* __restrict__ f, real* __restrict__ 
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % P.nx), y = (int)(c / P.nx);
         real v[9];
-        pull_row_walls(f, P, x, x == 0 ? P.nx - 1 : x - 1, x == P.nx - 1 ? 0 : x + 1, y, v);
+        pull_row_ext<true>(f, P, x, x == 0 ? P.nx - 1 : x - 1, x == P.nx - 1 ? 0 : x + 1, y, v);
         const real r = sum9(v);
         rho[c] = r;
         aux[c] = model == 0 ? pseudo_psi(r, P) : r;
@@ -317,7 +402,7 @@ __global__ void mu_walls_kernel(const real* __restrict__ rho, real* __restrict__
     const long long n = (long long)P.nx * P.ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         real rn[9];
-        gather8_walls(rho, (int)(c % P.nx), (int)(c / P.nx), P.nx, P.ny, rn);
+        gather8_ext(rho, (int)(c % P.nx), (int)(c / P.nx), P.nx, P.ny, true, rn);
         mu[c] = fe_mu(rn[0], rn, P);
     }
 }
@@ -335,8 +420,8 @@ __global__ void walls_complete_kernel(real* __restrict__ f, const real* __restri
         const int x = top ? k - nx : k, y = top ? ny - 1 : 0;
         const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
         real v[9], an[9];
-        pull_row_walls(f, P, x, xm, xp, y, v);
-        gather8_walls(aux, x, y, nx, ny, an);
+        pull_row_ext<true>(f, P, x, xm, xp, y, v);
+        gather8_ext(aux, x, y, nx, ny, true, an);
         const long long c = (long long)y * nx + x;
         const real Fx = (model == 0 ? an[0] : -rho[c]) * grad_x(an) + P.fx;
         wall_fill(v, top, real(-0.5) * Fx, real(-0.5) * P.fy);
@@ -355,24 +440,26 @@ __global__ void walls_complete_kernel(real* __restrict__ f, const real* __restri
     }
 }
 
-// u of Eq. (6b) of the completed state, mirrored neighbour fields (the wall-normal interaction
-// force vanishes at wall nodes, so u = 0 there up to rounding).
+// u of Eq. (6b) with the total force: walls -- of the completed state, mirrored neighbour
+// fields (the wall-normal interaction force vanishes at wall nodes, so u = 0 there up to
+// rounding); D.rho_ave -- the drive of the state included.
 template <typename real>
-__global__ void velocity_walls_kernel(const real* __restrict__ f, const real* __restrict__ rho,
-                                      const real* __restrict__ aux, real* __restrict__ ux, real* __restrict__ uy,
-                                      const StepParams<real> P, int model) {
+__global__ void velocity_ext_kernel(const real* __restrict__ f, const real* __restrict__ rho,
+                                    const real* __restrict__ aux, real* __restrict__ ux, real* __restrict__ uy,
+                                    const StepParams<real> P, int model, int walls, const Drive<real> D) {
     const long long n = (long long)P.nx * P.ny;
+    const real rave = D.rho_ave ? real(*D.rho_ave) : real(0);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % P.nx), y = (int)(c / P.nx);
         real v[9], an[9];
         pull_cell(f, P.pitch, x, y, P.nx, P.ny, v);
-        gather8_walls(aux, x, y, P.nx, P.ny, an);
+        gather8_ext(aux, x, y, P.nx, P.ny, walls != 0, an);
         const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
         const real gx = (an[1] - an[3]) * w1 + ((an[5] - an[7]) + (an[8] - an[6])) * w2;
         const real gy = (an[2] - an[4]) * w1 + ((an[5] - an[7]) + (an[6] - an[8])) * w2;
         const real r = rho[c];
         const real s = model == 0 ? an[0] : -r;
-        const real Fx = s * gx + P.fx, Fy = s * gy + P.fy;
+        const real Fx = s * gx + (D.rho_ave ? with_drive(P, D, x, r, rave).fx : P.fx), Fy = s * gy + P.fy;
         const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
         const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
         ux[c] = (jx + real(0.5) * Fx) / r;

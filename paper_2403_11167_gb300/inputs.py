@@ -17,6 +17,8 @@ Recipes (the paper initialises every run from f = f^eq(rho0, u = 0), Secs. 5.3-5
   liquid in the top half, rho(x, y) = rho_v + (rho_l - rho_v)/2 [1 + tanh(2(y - h(x))/W0)]
   with the interface at h(x) = (ny - 1)/2 + amp sin(2 pi x / nx) (amp = 0: the paper's flat
   interface; amp > 0 gives parity runs x-gradients).
+* ``two_droplets`` -- the droplet pair of Sec. 5.4: rho = rho_v + (rho_l - rho_v)/2
+  sum_k [1 - tanh(2(r_k - R)/W0)], r_k measured from each centre (well-separated droplets).
 """
 import numpy as np
 
@@ -48,6 +50,16 @@ def plate_channel(nx: int, ny: int, rho_v: float, rho_l: float, w0: float = 5.0,
     yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
     h = (ny - 1) / 2.0 + amp * np.sin(2.0 * np.pi * xx / nx)
     return rho_v + 0.5 * (rho_l - rho_v) * (1.0 + np.tanh(2.0 * (yy - h) / w0))
+
+
+def two_droplets(nx: int, ny: int, centres, radius: float, rho_v: float, rho_l: float,
+                 w0: float = 5.0) -> np.ndarray:
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    rho = np.full((ny, nx), rho_v)
+    for cx, cy in centres:
+        r = np.sqrt((xx - cx) ** 2 + (yy - cy) ** 2)
+        rho += 0.5 * (rho_l - rho_v) * (1.0 - np.tanh(2.0 * (r - radius) / w0))
+    return rho
 
 
 def calibration_sweep(n: int = 512, seed: int = 11167, step_range=(5000, 20000), w0: float = 5.0):

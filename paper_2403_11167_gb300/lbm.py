@@ -109,6 +109,8 @@ def _lib():
                             ctypes.POINTER(vp)], ctypes.c_int),
             "lbm_derived": ([vp, P, T], ctypes.c_int),
             "lbm_set_density": ([vp, dp], ctypes.c_int),
+            "lbm_set_drive": ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong],
+                              ctypes.c_int),
             "lbm_set_density_device": ([vp, vp], ctypes.c_int),
             "lbm_set_populations": ([vp, dp], ctypes.c_int),
             "lbm_get_populations": ([vp, dp], ctypes.c_int),
@@ -281,6 +283,10 @@ class Context:
         _check(_lib().lbm_get_populations_at(self.h, len(xs), xs.ctypes.data_as(ip), ys.ctypes.data_as(ip),
                                              _dptr(out)), "lbm_get_populations_at")
         return out
+
+    def set_drive(self, ax_lo: float, ax_hi: float, x_split: float, t_on: int):
+        """Droplet-collision drive of Sec. 5.4 (lbm_set_drive)."""
+        _check(_lib().lbm_set_drive(self.h, float(ax_lo), float(ax_hi), float(x_split), int(t_on)), "lbm_set_drive")
 
     def step(self, n: int):
         _check(_lib().lbm_step(self.h, int(n)), "lbm_step")
