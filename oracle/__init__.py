@@ -51,6 +51,8 @@ class Params(ctypes.Structure):
         ("walls", ctypes.c_double),
         ("drive", ctypes.c_double), ("drive_ax_lo", ctypes.c_double),
         ("drive_ax_hi", ctypes.c_double), ("drive_x_split", ctypes.c_double),
+        ("A", ctypes.c_double), ("g", ctypes.c_double), ("rho_g", ctypes.c_double),
+        ("y_ref", ctypes.c_double),
     ]
 
 
@@ -59,7 +61,7 @@ def make_params(**kw) -> Params:
     d = dict(a=0.5, b=4.0, R=1.0, T=0.0, G=-1.0, tau_rho=1.0, tau_e=1.0, tau_zeta=1.0,
              tau_j=1.0, tau_q=1.0, tau_nu=1.0, kappa_P=1.0, kappa_Li=0.0, sigma_Li=0.0,
              kappa=0.5, fx=0.0, fy=0.0, walls=0.0, drive=0.0, drive_ax_lo=0.0, drive_ax_hi=0.0,
-             drive_x_split=0.0)
+             drive_x_split=0.0, A=0.0, g=0.0, rho_g=0.0, y_ref=0.0)
     unknown = set(kw) - set(d)
     if unknown:
         raise KeyError(f"unknown oracle parameter(s): {sorted(unknown)}")
@@ -80,6 +82,8 @@ def lib():
         L.orc_run.argtypes = [ctypes.c_int, pp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_long, ctypes.c_int]
         L.orc_run.restype = ctypes.c_long
         L.orc_init.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+        L.orc_init_iwb.argtypes = [pp, ctypes.c_int, ctypes.c_int, dp, dp]
+        L.orc_feq_iwb.argtypes = [ctypes.c_double] * 8 + [dp]
         L.orc_macro.argtypes = [ctypes.c_int, pp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
         L.orc_macro.restype = ctypes.c_int
         L.orc_feq.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
@@ -121,6 +125,23 @@ def init(model: int, rho0: np.ndarray) -> np.ndarray:
     ny, nx = rho0.shape
     f = np.zeros((9, ny, nx))
     lib().orc_init(model, nx, ny, _ptr(rho0), _ptr(f))
+    return f
+
+
+def feq_iwb(rho, ux, uy, pg=0.0, A=0.0, Sxx=0.0, Sxy=0.0, Syy=0.0) -> np.ndarray:
+    """Eq. (20) in full at one cell (p_g, A and the strain rate S)."""
+    out = np.zeros(9)
+    lib().orc_feq_iwb(rho, ux, uy, pg, A, Sxx, Sxy, Syy, _ptr(out))
+    return out
+
+
+def init_iwb(p: Params, rho0: np.ndarray) -> np.ndarray:
+    """Free-energy populations f = f^eq of Eq. (20) at rest with the gravitational reference
+    pressure p_g = rho_0 g (y - y_ref) of p, shape (9, ny, nx)."""
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    ny, nx = rho0.shape
+    f = np.zeros((9, ny, nx))
+    lib().orc_init_iwb(ctypes.byref(p), nx, ny, _ptr(rho0), _ptr(f))
     return f
 
 

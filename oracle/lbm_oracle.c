@@ -69,6 +69,9 @@ typedef struct {
     double walls;       /* 0: periodic in y; 1: no-slip walls on rows 0 and ny-1 (Sec. 5.3) */
     double drive;       /* 1: add the droplet-collision force of Sec. 5.4 (drive_force) */
     double drive_ax_lo, drive_ax_hi, drive_x_split;
+    double A;           /* FE viscosity-tuning term of Eqs. (20), (23) */
+    double g, rho_g, y_ref; /* FE gravity (acting along -y), reference density rho_0 and the
+                               reference height of p_g = rho_0 g (y - y_ref) (Eqs. 20, 21) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -176,12 +179,38 @@ static void feq_standard(double rho, double ux, double uy, double feq[Q9]) {
 }
 
 /* Eq. (20) with A = 0 and p_g = 0: improved well-balanced equilibrium. */
-static void feq_wellbalanced(double rho, double ux, double uy, double feq[Q9]) {
-    double uu = ux * ux + uy * uy;
-    feq[0] = rho - WI[0] * rho * uu / (2.0 * CS2);
+/* Eq. (20) in full: p_g the gravitational reference pressure, A the viscosity-tuning term,
+ * S_ab = d_a u_b + d_b u_a (Sxx, Sxy, Syy).  With X = u u + c_s^2 A S,
+ *   f_0 = rho - (1 - w_0) p_g / c_s^2 - w_0 rho tr(X) / (2 c_s^2)
+ *   f_i = w_i p_g / c_s^2 + w_i rho [c_i.u / c_s^2 + (c_i.X.c_i - c_s^2 tr X) / (2 c_s^4)]
+ * (w_0 rho c_s^2 A tr(S) / (2 c_s^2) = w_0 rho A d_g u_g, the printed f_0 term). */
+static void feq_iwb(double rho, double ux, double uy, double pg, double A, double Sxx, double Sxy, double Syy,
+                    double feq[Q9]) {
+    const double Xxx = ux * ux + CS2 * A * Sxx, Xyy = uy * uy + CS2 * A * Syy, Xxy = ux * uy + CS2 * A * Sxy;
+    const double trX = Xxx + Xyy;
+    feq[0] = rho - (1.0 - WI[0]) * pg / CS2 - WI[0] * rho * trX / (2.0 * CS2);
     for (int i = 1; i < Q9; ++i) {
         double cu = CX[i] * ux + CY[i] * uy;
-        feq[i] = WI[i] * rho * (cu / CS2 + (cu * cu - CS2 * uu) / (2.0 * CS2 * CS2));
+        double cXc = CX[i] * CX[i] * Xxx + 2.0 * CX[i] * CY[i] * Xxy + CY[i] * CY[i] * Xyy;
+        feq[i] = WI[i] * pg / CS2 + WI[i] * rho * (cu / CS2 + (cXc - CS2 * trX) / (2.0 * CS2 * CS2));
+    }
+}
+
+/* Eq. (20) with A = 0 and p_g = 0. */
+static void feq_wellbalanced(double rho, double ux, double uy, double feq[Q9]) {
+    feq_iwb(rho, ux, uy, 0.0, 0.0, 0.0, 0.0, 0.0, feq);
+}
+
+/* p_g = rho_0 g (y - y_ref) of Eq. (20). */
+static double p_grav(const orc_params* p, int y) { return p->rho_g * p->g * ((double)y - p->y_ref); }
+
+/* FE initialisation with gravity: f = f^eq of Eq. (20) at rest, p_g included. */
+void orc_init_iwb(const orc_params* p, int nx, int ny, const double* rho0, double* f) {
+    size_t N = (size_t)nx * ny;
+    for (size_t c = 0; c < N; ++c) {
+        double feq[Q9];
+        feq_iwb(rho0[c], 0.0, 0.0, p_grav(p, (int)(c / nx)), 0.0, 0.0, 0.0, 0.0, feq);
+        for (int i = 0; i < Q9; ++i) f[(size_t)i * N + c] = feq[i];
     }
 }
 
@@ -266,9 +295,8 @@ static void lambda_diag(const orc_params* p, double L[Q9]) {
  * body force alone (the mirrored neighbours cancel the interaction part), so a first fill
  * with Jy = -fy/2 and Jx = 0 fixes rho exactly; once the forces are known the fill is
  * repeated with Jx = -Fx/2. */
-static void wall_fill(const orc_params* p, int nx, int ny, double* f, const double* Fx) {
+static void wall_fill(const orc_params* p, int nx, int ny, double* f, const double* Fx, const double* Fy) {
     size_t N = (size_t)nx * ny;
-    const double Jy = -p->fy / 2.0;
     for (int side = 0; side < 2; ++side) {
         const int y = side == 0 ? 0 : ny - 1;
         for (int x = 0; x < nx; ++x) {
@@ -276,6 +304,7 @@ static void wall_fill(const orc_params* p, int nx, int ny, double* f, const doub
             double* g[Q9];
             for (int i = 0; i < Q9; ++i) g[i] = &f[(size_t)i * N + c];
             const double Jx = Fx ? -Fx[c] / 2.0 : 0.0;
+            const double Jy = Fy ? -Fy[c] / 2.0 : -p->fy / 2.0;
             const double d13 = *g[1] - *g[3];
             if (side == 0) {
                 *g[2] = *g[4] + 2.0 / 3.0 * Jy;
@@ -315,7 +344,7 @@ static int pp_fields(const orc_params* p, int nx, int ny, double* f, double* rho
                      double* psi, double* Fx, double* Fy, double* ux, double* uy) {
     size_t N = (size_t)nx * ny;
     int bad = 0;
-    if (p->walls != 0.0) wall_fill(p, nx, ny, f, NULL);
+    if (p->walls != 0.0) wall_fill(p, nx, ny, f, NULL, NULL);
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (long c = 0; c < (long)N; ++c) {
         double s = 0.0;
@@ -335,7 +364,7 @@ static int pp_fields(const orc_params* p, int nx, int ny, double* f, double* rho
             Fx[c] = fix + p->fx + drive_force(p, x, rho[c], rave);
             Fy[c] = is_wall_row(p, y, ny) ? p->fy : fiy + p->fy;
         }
-    if (p->walls != 0.0) wall_fill(p, nx, ny, f, Fx);
+    if (p->walls != 0.0) wall_fill(p, nx, ny, f, Fx, NULL);
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
@@ -435,13 +464,28 @@ static double stencil_lap(const double* phi, int nx, int ny, int walls, int x, i
     return 2.0 / CS2 * s;
 }
 
+/* Eq. (24) gradient of a velocity component.  Beyond a no-slip wall the velocity is the
+ * negative of the mirrored row's (odd extension through u = 0 at the wall node). */
+static void stencil_grad_vel(const double* phi, int nx, int ny, int walls, int x, int y, double* gx, double* gy) {
+    double sx = 0.0, sy = 0.0;
+    for (int i = 0; i < Q9; ++i) {
+        const int yy = y + CY[i];
+        const double sgn = (walls && (yy < 0 || yy > ny - 1)) ? -1.0 : 1.0;
+        double v = sgn * phi[yrow(yy, ny, walls) * nx + wrap(x + CX[i], nx)];
+        sx += WI[i] * v * CX[i];
+        sy += WI[i] * v * CY[i];
+    }
+    *gx = sx / CS2;
+    *gy = sy / CS2;
+}
+
 /* Density, chemical potential, gradients, force and velocity of the FE model. */
 static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho,
                      double* mu, double* Fx, double* Fy, double* ux, double* uy, double* drx,
                      double* dry) {
     size_t N = (size_t)nx * ny;
     int bad = 0;
-    if (p->walls != 0.0) wall_fill(p, nx, ny, f, NULL);
+    if (p->walls != 0.0) wall_fill(p, nx, ny, f, NULL, NULL);
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (long c = 0; c < (long)N; ++c) {
         double s = 0.0;
@@ -450,6 +494,30 @@ static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho
         if (!(s > 0.0) || !(p->b * s / 4.0 < 1.0)) bad = 1;
     }
     if (bad) return -1;
+    if (p->walls != 0.0 && p->g != 0.0) {
+        /* a wall node's normal force includes gravity, -(rho - rho_0) g, which depends on its
+         * own density: sum_i f_i = K + Jy (bottom) or K - Jy (top), Jy = -F_y/2, solved for
+         * rho in closed form from the first fill's density (Jy = -fy/2) and filled again */
+        for (int side = 0; side < 2; ++side) {
+            const int y = side == 0 ? 0 : ny - 1;
+            const double sg = side == 0 ? 1.0 : -1.0;
+            for (int x = 0; x < nx; ++x) {
+                size_t c = (size_t)y * nx + x;
+                const double rw = (rho[c] - sg * p->rho_g * p->g / 2.0) / (1.0 - sg * p->g / 2.0);
+                Fy[c] = p->fy - (rw - p->rho_g) * p->g;
+            }
+        }
+        wall_fill(p, nx, ny, f, NULL, Fy);
+        for (int side = 0; side < 2; ++side) {
+            const int y = side == 0 ? 0 : ny - 1;
+            for (int x = 0; x < nx; ++x) {
+                size_t c = (size_t)y * nx + x;
+                double s = 0.0;
+                for (int i = 0; i < Q9; ++i) s += f[(size_t)i * N + c];
+                rho[c] = s;
+            }
+        }
+    }
     const double rave = p->drive != 0.0 ? domain_mean(rho, N) : 0.0;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
@@ -464,14 +532,15 @@ static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho
             double gmx, gmy;
             stencil_grad(mu, nx, ny, p->walls != 0.0, x, y, &gmx, &gmy);
             stencil_grad(rho, nx, ny, p->walls != 0.0, x, y, &drx[c], &dry[c]);
+            const double Fg = -(rho[c] - p->rho_g) * p->g;  /* buoyancy F_g of Eq. (21) */
             Fx[c] = -rho[c] * gmx + p->fx + drive_force(p, x, rho[c], rave);
-            Fy[c] = -rho[c] * gmy + p->fy;
+            Fy[c] = -rho[c] * gmy + p->fy + Fg;
             if (is_wall_row(p, y, ny)) {  /* mirrored neighbours: no normal gradient */
-                Fy[c] = p->fy;
+                Fy[c] = p->fy + Fg;
                 dry[c] = 0.0;
             }
         }
-    if (p->walls != 0.0) wall_fill(p, nx, ny, f, Fx);
+    if (p->walls != 0.0) wall_fill(p, nx, ny, f, Fx, Fy);
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
@@ -501,11 +570,22 @@ static int fe_step(const orc_params* p, int nx, int ny, double* f, double* fnew,
             size_t c = (size_t)y * nx + x;
             double fc[Q9], feq[Q9], Fi[Q9], m[Q9], meq[Q9], MF[Q9], dm[Q9];
             for (int i = 0; i < Q9; ++i) fc[i] = f[(size_t)i * N + c];
-            feq_wellbalanced(rho[c], ux[c], uy[c], feq);
-            /* Eq. (21), d = 2, grad p_g = 0:
+            /* Eq. (20) with S_ab from the Eq. (24) gradients of u (only when A != 0) */
+            double Sxx = 0.0, Sxy = 0.0, Syy = 0.0;
+            if (p->A != 0.0) {
+                double dxux, dyux, dxuy, dyuy;
+                stencil_grad_vel(ux, nx, ny, p->walls != 0.0, x, y, &dxux, &dyux);
+                stencil_grad_vel(uy, nx, ny, p->walls != 0.0, x, y, &dxuy, &dyuy);
+                Sxx = 2.0 * dxux;
+                Syy = 2.0 * dyuy;
+                Sxy = dxuy + dyux;
+            }
+            feq_iwb(rho[c], ux[c], uy[c], p_grav(p, y), p->A, Sxx, Sxy, Syy, feq);
+            /* Eq. (21), d = 2, grad p_g = (0, rho_0 g):
              * F_i = w_i [ c_a F_a / c_s^2
-             *           + (c_a c_b - c_s^2 d_ab) u_a (F_b + c_s^2 d_b rho) / c_s^4
+             *           + (c_a c_b - c_s^2 d_ab) u_a (F_b - d_b p_g + c_s^2 d_b rho) / c_s^4
              *           + 1/2 (|c|^2 / c_s^2 - d) u_g d_g rho ] */
+            const double dpg[2] = {0.0, p->rho_g * p->g};
             double u[2] = {ux[c], uy[c]}, F[2] = {Fx[c], Fy[c]}, gr[2] = {drx[c], dry[c]};
             double ugr = u[0] * gr[0] + u[1] * gr[1];
             for (int i = 0; i < Q9; ++i) {
@@ -515,7 +595,7 @@ static int fe_step(const orc_params* p, int nx, int ny, double* f, double* fnew,
                 for (int a = 0; a < 2; ++a)
                     for (int b = 0; b < 2; ++b) {
                         double d = (a == b) ? 1.0 : 0.0;
-                        t2 += (ci[a] * ci[b] - CS2 * d) * u[a] * (F[b] + CS2 * gr[b]);
+                        t2 += (ci[a] * ci[b] - CS2 * d) * u[a] * (F[b] - dpg[b] + CS2 * gr[b]);
                     }
                 t2 /= CS2 * CS2;
                 double c2 = ci[0] * ci[0] + ci[1] * ci[1];
@@ -638,6 +718,12 @@ void orc_feq(int model, double rho, double ux, double uy, double* feq) {
         feq_standard(rho, ux, uy, feq);
     else
         feq_wellbalanced(rho, ux, uy, feq);
+}
+
+/* Eq. (20) in full for given rho, u, p_g, A and S (Sxx, Sxy, Syy). */
+void orc_feq_iwb(double rho, double ux, double uy, double pg, double A, double Sxx, double Sxy, double Syy,
+                 double* feq) {
+    feq_iwb(rho, ux, uy, pg, A, Sxx, Sxy, Syy, feq);
 }
 
 /* Population-space forcing of the FE model, Eq. (21), for given u, F, grad rho. */
