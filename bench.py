@@ -326,6 +326,22 @@ def run_walls(args, peak):
                     col[key]["f32_4096_frac_of_hbm_at_72B"] = BYTES_PER_CELL_F32 * nx * ny * n / sec / 1e9 / peak
                 ctx.close()
         out["collision_sec54"] = col
+        # full free-energy model (A != 0: strain rate of u at the neighbours), FP32 droplet
+        p = lbm.lbm_params_default(1, precision=lbm.LBM_F32, a=0.25, Tr=0.8, tau_nu=1.0, tau_e=0.9, A=0.15)
+        ctx = lbm.Context(p, size, size, stream=stream)
+        _, th = ctx.derived()
+        ctx.set_density(inputs.droplet(size, size, size / 4, th.rho_v, th.rho_l))
+        ctx.step(64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.step(256)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3 / 256
+        out["free_energy_A_f32"] = {"kernel": "fe_step_iwb", "mlups": size * size / sec / 1e6,
+                                    "frac_of_hbm_at_72B": BYTES_PER_CELL_F32 * size * size / sec / 1e9 / peak}
+        ctx.close()
     return out
 
 

@@ -73,7 +73,10 @@ typedef enum { LBM_GEOMETRY_FLAT = 0, LBM_GEOMETRY_DROPLET = 1 } lbm_geometry;
  *               has the interface width and surface tension of the free-energy model
  *               with kappa = match_kappa (Sec. 3, Appendix B, Eqs. 26, S44, S46).
  *   kappa       free-energy gradient coefficient (mu = mu_b - kappa lap rho); NaN -> 0.5.
- *   A           viscosity-tuning term of Eq. (20); only A = 0 is supported.
+ *   A           viscosity-tuning term of the free-energy equilibrium, Eq. (20) (the strain-
+ *               rate terms); nu = c_s^2 (tau_nu - 1/2 - A) must be positive (Eq. 23).  Free
+ *               energy only (A != 0 with the pseudopotential model: LBM_ERR_UNSUPPORTED).
+ *               A != 0 runs the full free-energy kernel (direct loads, one more ring level).
  *   body_fx/fy  constant body force added to the total force of either model. */
 typedef struct {
     int model;       /* lbm_model */
@@ -159,6 +162,16 @@ int lbm_set_density_device(lbm_ctx* ctx, const void* rho0_device);
 /* Set / read the raw populations (host, FP64, [9][ny][nx], Eq. 2 order). */
 int lbm_set_populations(lbm_ctx* ctx, const double* f);
 int lbm_get_populations(lbm_ctx* ctx, double* f);
+
+/* Gravity of the free-energy model (Eqs. 20, 21): acceleration g along -y, reference density
+ * rho_ref, reference height y_ref.  The equilibrium carries p_g = rho_ref g (y - y_ref), the
+ * forcing's second-order term -grad p_g, and the force the buoyancy -(rho - rho_ref) g.  With
+ * rho_ref != 0 the lattice needs walls in y (p_g would jump at a periodic wrap); rho_ref = 0
+ * is plain weight, -rho g, and works on periodic lattices.  Call before lbm_set_density (its
+ * equilibrium includes p_g).  g = 0 switches gravity off.  Errors: LBM_ERR_ARG for a
+ * non-finite value; LBM_ERR_UNSUPPORTED for the pseudopotential model or rho_ref != 0 without
+ * walls.  Synchronises the stream. */
+int lbm_set_gravity(lbm_ctx* ctx, double g, double rho_ref, double y_ref);
 
 /* Droplet-collision drive of Sec. 5.4: from now on the collision of every state at time
  * t > t_on (t = steps taken since lbm_set_density) adds to the x force of each cell

@@ -107,6 +107,8 @@ struct lbm_ctx {
     bool use_tma;
     bool walls;          // no-slip walls on rows 0 and ny-1 (direct wall kernels)
     bool drive;          // droplet-collision drive configured (lbm_set_drive)
+    bool grav;           // gravity configured (lbm_set_gravity; free-energy model)
+    double g, rho_g, y_ref;
     double drive_lo, drive_hi, drive_split;
     long long drive_t_on;
     double* h_pinned;    // 8 doubles, pinned
@@ -205,7 +207,9 @@ extern "C" int lbm_resolve_params(const lbm_params* in, lbm_params* out, lbm_the
     if (p.precision != LBM_F32 && p.precision != LBM_F64) return LBM_ERR_ARG;
     if (!(p.a > 0 && p.b > 0 && p.R > 0 && p.Tr > 0 && p.Tr < 1)) return LBM_ERR_ARG;
     if (!(p.tau_nu > 0.5)) return LBM_ERR_ARG;
-    if (p.A != 0.0) return LBM_ERR_UNSUPPORTED;
+    if (!std::isfinite(p.A)) return LBM_ERR_ARG;
+    if (p.A != 0.0 && p.model == LBM_PSEUDOPOTENTIAL) return LBM_ERR_UNSUPPORTED;  // A is a FE term (Eq. 20)
+    if (!(p.tau_nu - 0.5 - p.A > 0)) return LBM_ERR_ARG;  // nu = c_s^2 (tau_nu - 1/2 - A) > 0 (Eq. 23)
     if (!std::isfinite(p.body_fx) || !std::isfinite(p.body_fy)) return LBM_ERR_ARG;
     const bool pp = p.model == LBM_PSEUDOPOTENTIAL;
     if (!(p.tau_j > 0)) p.tau_j = 1.0;
@@ -454,6 +458,8 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     }
     c->graph[0][0] = c->graph[0][1] = c->graph[1][0] = c->graph[1][1] = nullptr;
     c->drive = false;
+    c->grav = false;
+    c->g = c->rho_g = c->y_ref = 0.0;
     c->cur = 0;
     c->step = 0;
     c->status = LBM_OK;
@@ -566,7 +572,43 @@ static int launch_step_driven(lbm_ctx* c, int src) {
     return LBM_OK;
 }
 
+// Free-energy contexts with A != 0 or gravity run the full model's kernel.
+static bool uses_iwb(const lbm_ctx* c) {
+    return c->prm.model == LBM_FREE_ENERGY && (c->prm.A != 0.0 || c->grav);
+}
+
+template <typename real>
+static lbmk::Ext<real> ext_terms(const lbm_ctx* c) {
+    lbmk::Ext<real> e;
+    e.on = uses_iwb(c) ? 1 : 0;
+    e.A = (real)c->prm.A;
+    e.g = (real)(c->grav ? c->g : 0.0);
+    e.rho_g = (real)(c->grav ? c->rho_g : 0.0);
+    e.y_ref = (real)c->y_ref;
+    return e;
+}
+
+template <typename real, int TX>
+static void launch_iwb(lbm_ctx* c, int src, bool driven, const lbmk::StepParams<real>& sp) {
+    const lbmk::Drive<real> d = driven ? launch_drive<real>(c, src) : no_drive<real>();
+    dim3 grid((c->nx + TX - 1) / TX, (c->ny + c->rows - 1) / c->rows);
+    const real* fin = static_cast<const real*>(c->f[src]);
+    real* fout = static_cast<real*>(c->f[src ^ 1]);
+    if (c->walls)
+        lbmk::fe_step_iwb<real, TX, true><<<grid, TX + 32, 0, c->stream>>>(fin, fout, sp, d, ext_terms<real>(c));
+    else
+        lbmk::fe_step_iwb<real, TX, false><<<grid, TX + 32, 0, c->stream>>>(fin, fout, sp, d, ext_terms<real>(c));
+}
+
 static int launch_step(lbm_ctx* c, int src, bool driven = false) {
+    if (uses_iwb(c)) {
+        if (c->prec == LBM_F32)
+            launch_iwb<float, kTXf>(c, src, driven, c->spf);
+        else
+            launch_iwb<double, kTXd>(c, src, driven, c->spd);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
     if (driven) return launch_step_driven(c, src);
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
@@ -696,6 +738,24 @@ extern "C" int lbm_step(lbm_ctx* c, long long nsteps) {
     return LBM_OK;
 }
 
+extern "C" int lbm_set_gravity(lbm_ctx* c, double g, double rho_ref, double y_ref) {
+    if (!c || !std::isfinite(g) || !std::isfinite(rho_ref) || !std::isfinite(y_ref)) return LBM_ERR_ARG;
+    if (c->prm.model != LBM_FREE_ENERGY) return LBM_ERR_UNSUPPORTED;
+    if (rho_ref != 0.0 && !c->walls) return LBM_ERR_UNSUPPORTED;  // p_g would jump at the periodic wrap
+    CK(cudaStreamSynchronize(c->stream));
+    c->grav = g != 0.0;
+    c->g = g;
+    c->rho_g = rho_ref;
+    c->y_ref = y_ref;
+    for (int i = 0; i < 2; ++i)
+        for (int m = 0; m < 2; ++m)
+            if (c->graph[i][m]) {
+                cudaGraphExecDestroy(c->graph[i][m]);
+                c->graph[i][m] = nullptr;
+            }
+    return LBM_OK;
+}
+
 extern "C" int lbm_set_drive(lbm_ctx* c, double ax_lo, double ax_hi, double x_split, long long t_on) {
     if (!c || !std::isfinite(ax_lo) || !std::isfinite(ax_hi) || !std::isfinite(x_split)) return LBM_ERR_ARG;
     if (c->walls) return LBM_ERR_UNSUPPORTED;
@@ -717,6 +777,23 @@ extern "C" int lbm_set_drive(lbm_ctx* c, double ax_lo, double ax_hi, double x_sp
 template <typename src_t>
 static int launch_init(lbm_ctx* c, const src_t* rho0_dev) {
     const int model = c->prm.model;
+    if (model == LBM_FREE_ENERGY && c->grav && c->rho_g != 0.0) {
+        // equilibrium at rest with the gravitational reference pressure p_g of Eq. (20)
+        const double coef = c->rho_g * c->g;
+        if (c->prec == LBM_F32)
+            lbmk::init_iwb_kernel<float, src_t><<<kRedBlocks, 256, 0, c->stream>>>(
+                rho0_dev, (float*)c->f[0], c->nx, c->ny, c->pitch, coef, c->y_ref);
+        else
+            lbmk::init_iwb_kernel<double, src_t><<<kRedBlocks, 256, 0, c->stream>>>(
+                rho0_dev, (double*)c->f[0], c->nx, c->ny, c->pitch, coef, c->y_ref);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        c->cur = 0;
+        c->step = 0;
+        c->status = LBM_OK;
+        c->ready = true;
+        return LBM_OK;
+    }
     if (c->prec == LBM_F32)
         lbmk::init_kernel<float, src_t>
             <<<kRedBlocks, 256, 0, c->stream>>>(rho0_dev, (float*)c->f[0], model, c->nx, c->ny, c->pitch);
@@ -854,20 +931,21 @@ static int compute_fields(lbm_ctx* c, const lbmk::StepParams<real>& sp) {
     real* uy = ux + n;
     const real* f = static_cast<const real*>(c->f[c->cur]);
     const int model = c->prm.model;
-    if (c->walls || driven_at(c, c->step)) {
+    if (c->walls || driven_at(c, c->step) || uses_iwb(c)) {
         real* fw = static_cast<real*>(c->f[c->cur]);
+        const lbmk::Ext<real> ex = ext_terms<real>(c);
         if (c->walls) {
-            lbmk::rho_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, sp, model);
+            lbmk::rho_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, sp, model, ex);
             if (model == LBM_FREE_ENERGY) lbmk::mu_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
             lbmk::walls_complete_kernel<real>
-                <<<(2 * c->nx + 255) / 256, 256, 0, c->stream>>>(fw, rho, aux, sp, model);
+                <<<(2 * c->nx + 255) / 256, 256, 0, c->stream>>>(fw, rho, aux, sp, model, ex);
         } else {
             lbmk::rho_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(f, rho, aux, sp, model);
             if (model == LBM_FREE_ENERGY) lbmk::mu_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
         }
         const lbmk::Drive<real> d = driven_at(c, c->step) ? launch_drive<real>(c, c->cur) : no_drive<real>();
         lbmk::velocity_ext_kernel<real>
-            <<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, ux, uy, sp, model, c->walls ? 1 : 0, d);
+            <<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, ux, uy, sp, model, c->walls ? 1 : 0, d, ex);
         CK(cudaGetLastError());
         return LBM_OK;
     }

@@ -24,6 +24,12 @@
 // force: it adds to the total force like the body force and stays out of the interaction
 // force of Eq. (32)'s sigma^Li term.
 //
+// Full free-energy model (fe_step_iwb): the viscosity-tuning term A of Eqs. (20)/(23), which
+// needs the strain rate of u and so u at the neighbours (one more ring level: rho -> mu -> u ->
+// collision), and gravity: p_g = rho_g g (y - y_ref) in the equilibrium, -grad p_g in the
+// forcing's second-order term, and the buoyancy F_g = -(rho - rho_g) g in the force (Eq. 21).
+// Beyond a wall, velocities are odd (u = 0 at the wall node).
+//
 // The kernels follow the direct step kernels of lbm_kernels.cuh (one column per thread,
 // shared-memory rings of the neighbour fields, one halo warp).  With WALLS the pulled rows
 // map through mirror_row, wall rows get the two fills, and a wall row's collision sees its
@@ -116,6 +122,26 @@ struct Drive {
     int x_split;
     real ax_lo, ax_hi;
 };
+
+// Full improved well-balanced free-energy terms (Eqs. 20, 21): the viscosity-tuning A and
+// gravity g along -y with reference density rho_g, p_g = rho_g g (y - y_ref).  on == 0: none.
+template <typename real>
+struct Ext {
+    int on;
+    real A, g, rho_g, y_ref;
+};
+
+// With gravity a wall node's normal force, fy - (rho - rho_g) g, depends on its own density:
+// sum_i f_i = K + Jy (bottom) or K - Jy (top) with Jy = -F_y/2.  Solved in closed form from
+// the density after the first fill (Jy = -fy/2), then filled again.
+template <typename real>
+__device__ __forceinline__ void wall_gravity_refill(real v[9], bool top, const StepParams<real>& P,
+                                                    const Ext<real>& E) {
+    const real rp = sum9(v);
+    const real sg = top ? real(-1) : real(1);
+    const real rw = (rp - sg * E.rho_g * E.g * real(0.5)) / (real(1) - sg * E.g * real(0.5));
+    wall_fill(v, top, real(0), real(-0.5) * (P.fy - (rw - E.rho_g) * E.g));
+}
 
 // Parameters of one cell's collision with the drive added to the body force.
 template <typename real>
@@ -314,6 +340,7 @@ __global__ void __launch_bounds__(TX + 32) fe_step_ext(const real* __restrict__ 
             rn[6] = rp[rc - 1];
             rn[7] = rm[rc - 1];
             rn[8] = rm[rc + 1];
+            rn[0] = r0[rc];  // every entry defined: the FP32 overload copies all nine
             s_mu[(r - 1) & 3][mc] = fe_mu(r0[rc], rn, P);
         }
         __syncthreads();
@@ -332,6 +359,8 @@ __global__ void __launch_bounds__(TX + 32) fe_step_ext(const real* __restrict__ 
             rn[1] = r0[rc + 1]; rn[2] = rp[rc]; rn[3] = r0[rc - 1]; rn[4] = rm[rc];
             rn[5] = rp[rc + 1]; rn[6] = rp[rc - 1]; rn[7] = rm[rc - 1]; rn[8] = rm[rc + 1];
             const real rho_c = r0[rc];
+            mn[0] = m0[mc];
+            rn[0] = rho_c;
             if (WALLS && (c == 0 || c == ny - 1)) {
                 // mu beyond the wall is mu of the mirrored row (the ring holds the value
                 // recomputed from mirrored rho, equal up to rounding order)
@@ -384,12 +413,13 @@ __device__ __forceinline__ void gather8_ext(const real* __restrict__ a, int x, i
 // rho (Eq. 6a, wall rows after the first fill) and aux = psi (P) or rho (FE).
 template <typename real>
 __global__ void rho_walls_kernel(const real* __restrict__ f, real* __restrict__ rho, real* __restrict__ aux,
-                                 const StepParams<real> P, int model) {
+                                 const StepParams<real> P, int model, const Ext<real> E) {
     const long long n = (long long)P.nx * P.ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % P.nx), y = (int)(c / P.nx);
         real v[9];
         pull_row_ext<true>(f, P, x, x == 0 ? P.nx - 1 : x - 1, x == P.nx - 1 ? 0 : x + 1, y, v);
+        if (E.on && E.g != real(0) && (y == 0 || y == P.ny - 1)) wall_gravity_refill(v, y != 0, P, E);
         const real r = sum9(v);
         rho[c] = r;
         aux[c] = model == 0 ? pseudo_psi(r, P) : r;
@@ -413,7 +443,8 @@ __global__ void mu_walls_kernel(const real* __restrict__ rho, real* __restrict__
 // own node's unknown slots.  aux = psi (P) or mu (FE).
 template <typename real>
 __global__ void walls_complete_kernel(real* __restrict__ f, const real* __restrict__ rho,
-                                      const real* __restrict__ aux, const StepParams<real> P, int model) {
+                                      const real* __restrict__ aux, const StepParams<real> P, int model,
+                                      const Ext<real> E) {
     const int nx = P.nx, ny = P.ny;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * nx; k += gridDim.x * blockDim.x) {
         const bool top = k >= nx;
@@ -424,7 +455,8 @@ __global__ void walls_complete_kernel(real* __restrict__ f, const real* __restri
         gather8_ext(aux, x, y, nx, ny, true, an);
         const long long c = (long long)y * nx + x;
         const real Fx = (model == 0 ? an[0] : -rho[c]) * grad_x(an) + P.fx;
-        wall_fill(v, top, real(-0.5) * Fx, real(-0.5) * P.fy);
+        const real Fy = P.fy - (E.on ? (rho[c] - E.rho_g) * E.g : real(0));
+        wall_fill(v, top, real(-0.5) * Fx, real(-0.5) * Fy);
         // f_i(x, y) = S_i(x - c_i): bottom unknowns 2 (0,1), 5 (1,1), 6 (-1,1) sit in row ny-1;
         // top unknowns 4 (0,-1), 7 (-1,-1), 8 (1,-1) in row 0
         const long long ro = top ? 0 : (long long)(ny - 1) * nx;
@@ -446,7 +478,8 @@ __global__ void walls_complete_kernel(real* __restrict__ f, const real* __restri
 template <typename real>
 __global__ void velocity_ext_kernel(const real* __restrict__ f, const real* __restrict__ rho,
                                     const real* __restrict__ aux, real* __restrict__ ux, real* __restrict__ uy,
-                                    const StepParams<real> P, int model, int walls, const Drive<real> D) {
+                                    const StepParams<real> P, int model, int walls, const Drive<real> D,
+                                    const Ext<real> E) {
     const long long n = (long long)P.nx * P.ny;
     const real rave = D.rho_ave ? real(*D.rho_ave) : real(0);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -459,11 +492,239 @@ __global__ void velocity_ext_kernel(const real* __restrict__ f, const real* __re
         const real gy = (an[2] - an[4]) * w1 + ((an[5] - an[7]) + (an[6] - an[8])) * w2;
         const real r = rho[c];
         const real s = model == 0 ? an[0] : -r;
-        const real Fx = s * gx + (D.rho_ave ? with_drive(P, D, x, r, rave).fx : P.fx), Fy = s * gy + P.fy;
+        const real Fx = s * gx + (D.rho_ave ? with_drive(P, D, x, r, rave).fx : P.fx);
+        const real Fy = s * gy + P.fy - (E.on ? (r - E.rho_g) * E.g : real(0));
         const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
         const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
         ux[c] = (jx + real(0.5) * Fx) / r;
         uy[c] = (jy + real(0.5) * Fy) / r;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Full improved well-balanced free-energy model (Eqs. 1, 6, 20, 21, 24, 29 with A != 0 and/or
+// gravity; walls and the drive as above).
+//
+// Collision of one cell: mn, rn -- mu and rho at x + c_i; uxn, uyn -- u at x + c_i (the
+// strain rate S_ab = d_a u_b + d_b u_a of Eq. 20 by the Eq. 24 gradient); Fxe, Fye -- the
+// external force (body force, drive, buoyancy F_g = -(rho - rho_g) g); pg -- p_g at the cell.
+// The moments of Eq. (20)'s extra terms: e^eq += rho A tr S + 6 p_g, zeta^eq -= rho A tr S +
+// 9 p_g, p_xx^eq += rho c_s^2 A (S_xx - S_yy), p_xy^eq += rho c_s^2 A S_xy; the forcing's
+// second-order term carries F - grad p_g + c_s^2 grad rho, grad p_g = (0, rho_g g).
+template <typename real>
+__device__ __forceinline__ void fe_collide_iwb(real v[9], real rho, const real mn[9], const real rn[9],
+                                               const real uxn[9], const real uyn[9], real Fxe, real Fye, real pg,
+                                               const StepParams<real>& P, const Ext<real>& E) {
+    const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
+    const real gmx = grad_x(mn);
+    const real gmy = (mn[2] - mn[4]) * w1 + ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2;
+    const real grx = grad_x(rn);
+    const real gry = (rn[2] - rn[4]) * w1 + ((rn[5] - rn[7]) + (rn[6] - rn[8])) * w2;
+    const real Fx = -rho * gmx + Fxe, Fy = -rho * gmy + Fye;
+    const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const real ux = (jx + real(0.5) * Fx) / rho;
+    const real uy = (jy + real(0.5) * Fy) / rho;
+    // S from the velocity stencil (Eq. 24)
+    const real dxux = grad_x(uxn), dxuy = grad_x(uyn);
+    const real dyux = (uxn[2] - uxn[4]) * w1 + ((uxn[5] - uxn[7]) + (uxn[6] - uxn[8])) * w2;
+    const real dyuy = (uyn[2] - uyn[4]) * w1 + ((uyn[5] - uyn[7]) + (uyn[6] - uyn[8])) * w2;
+    const real Sxx = real(2) * dxux, Syy = real(2) * dyuy, Sxy = dxuy + dyux;
+    const real rA = rho * E.A;
+    const real sax = (v[1] + v[2]) + (v[3] + v[4]);
+    const real sdg = (v[5] + v[6]) + (v[7] + v[8]);
+    const real e = -real(4) * v[0] - sax + real(2) * sdg;
+    const real z = real(4) * v[0] - real(2) * sax + sdg;
+    const real qx = real(2) * (v[3] - v[1]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const real qy = real(2) * (v[4] - v[2]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const real pxx = (v[1] + v[3]) - (v[2] + v[4]);
+    const real pxy = (v[5] + v[7]) - (v[6] + v[8]);
+    const real uu = ux * ux + uy * uy;
+    const real dpg = E.rho_g * E.g;  // d_y p_g
+    const real uG = ux * Fx + uy * (Fy - dpg);
+    const real s = ux * grx + uy * gry;  // u . grad rho
+    const real Gx = Fx + grx * real(1.0 / 3.0), Gy = Fy - dpg + gry * real(1.0 / 3.0);
+    const real fe = real(6) * uG + real(4) * s;
+    const real trS = Sxx + Syy;
+    const real e_eq = rho * (real(3) * uu - real(4)) + rA * trS + real(6) * pg;
+    const real z_eq = rho * (real(4) - real(3) * uu) - rA * trS - real(9) * pg;
+    const real pxx_eq = rho * (ux * ux - uy * uy) + rA * real(1.0 / 3.0) * (Sxx - Syy);
+    const real pxy_eq = rho * ux * uy + rA * real(1.0 / 3.0) * Sxy;
+    const real de = -P.s_e * (e - e_eq) + (real(1) - real(0.5) * P.s_e) * fe;
+    const real dz = -P.s_z * (z - z_eq) - (real(1) - real(0.5) * P.s_z) * fe;
+    const real dqx = -P.s_q * (qx + rho * ux) - (real(1) - real(0.5) * P.s_q) * Fx;
+    const real dqy = -P.s_q * (qy + rho * uy) - (real(1) - real(0.5) * P.s_q) * Fy;
+    const real dpxx = -P.s_nu * (pxx - pxx_eq) + (real(1) - real(0.5) * P.s_nu) * real(2) * (ux * Gx - uy * Gy);
+    const real dpxy = -P.s_nu * (pxy - pxy_eq) + (real(1) - real(0.5) * P.s_nu) * (ux * Gy + uy * Gx);
+    apply_dm(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+}
+
+// One column per thread plus a halo warp whose lanes 0..5 hold the columns x0-3, x0-2, x0-1,
+// x0+w, x0+w+1, x0+w+2.  Row pipeline of iteration r: pull row r+1; rho(r) into the rho ring;
+// mu(r-1) (columns x0-2 .. x0+w+1); u(r-2) (columns x0-1 .. x0+w; at a wall row after the
+// final fill, J = -F/2); collision of row r-3.  Rings: rho 8 rows, mu and u 4 rows.
+template <typename real, int TX, bool WALLS>
+__global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ fin, real* __restrict__ fout,
+                                                       const StepParams<real> P, const Drive<real> D,
+                                                       const Ext<real> E) {
+    __shared__ real s_rho[8][TX + 6];
+    __shared__ real s_mu[4][TX + 4];
+    __shared__ real s_ux[4][TX + 2];
+    __shared__ real s_uy[4][TX + 2];
+    const real s_rave = D.rho_ave ? real(*D.rho_ave) : real(0);
+    const int nx = P.nx, ny = P.ny;
+    const long long pitch = P.pitch;
+    const int x0 = blockIdx.x * TX;
+    const int w = min(TX, nx - x0);
+    const int y0 = blockIdx.y * P.rows;
+    const int y1 = min(y0 + P.rows, ny);
+    const int t = threadIdx.x;
+    const bool is_main = t < TX;
+    bool has_col, has_mu, has_u;
+    int off;  // column offset from x0
+    if (is_main) {
+        has_col = t < w;
+        has_mu = has_u = has_col;
+        off = t;
+    } else {
+        const int lane = t - TX;
+        has_col = lane < 6;
+        has_mu = lane >= 1 && lane <= 4;
+        has_u = lane == 2 || lane == 3;
+        off = lane < 3 ? lane - 3 : w + (lane - 3);
+    }
+    const int x = has_col ? wrap_idx(x0 + off, nx) : x0;
+    const int rc = off + 3, mc = off + 2, uc = off + 1;  // ring columns
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+    // pulled populations of one row (mapped), with the wall fills of the first kind
+    auto pull = [&](int r, real v[9]) {
+        const int y = stencil_row<WALLS>(r, ny);
+        pull_row_ext<WALLS>(fin, P, x, xm, xp, y, v);
+        if (WALLS && E.on && E.g != real(0) && (y == 0 || y == ny - 1)) wall_gravity_refill(v, y != 0, P, E);
+    };
+    // external force of a cell of row r (mapped row y) with density rho
+    auto ext_fx = [&](real rho) { return D.rho_ave ? with_drive(P, D, x, rho, s_rave).fx : P.fx; };
+    auto ext_fy = [&](real rho) { return P.fy - (E.on ? (rho - E.rho_g) * E.g : real(0)); };
+    real p0[9], p1[9], p2[9], p3[9];  // rows r-3, r-2, r-1, r
+    if (has_col) pull(y0 - 3, p3);
+#pragma unroll 1
+    for (int r = y0 - 3; r <= y1 + 2; ++r) {
+        real nxt[9];
+        if (has_col && r + 1 <= y1 + 2) pull(r + 1, nxt);
+        if (has_col) s_rho[r & 7][rc] = sum9(p3);
+        __syncthreads();
+        if (has_mu && r >= y0 - 1) {  // mu(r-1)
+            const real* rm = s_rho[(r - 2) & 7];
+            const real* r0 = s_rho[(r - 1) & 7];
+            const real* rp = s_rho[r & 7];
+            real rn[9];
+            rn[1] = r0[rc + 1]; rn[2] = rp[rc]; rn[3] = r0[rc - 1]; rn[4] = rm[rc];
+            rn[5] = rp[rc + 1]; rn[6] = rp[rc - 1]; rn[7] = rm[rc - 1]; rn[8] = rm[rc + 1];
+            rn[0] = r0[rc];  // every entry defined (the FP32 overload reads all nine)
+            s_mu[(r - 1) & 3][mc] = fe_mu<real>(r0[rc], rn, P);
+        }
+        __syncthreads();
+        if (has_u && r >= y0 + 1) {  // u(r-2) from this column's populations of row r-2 (p1)
+            const int cu = r - 2;
+            const real* mm = s_mu[(cu - 1) & 3];
+            const real* m0 = s_mu[cu & 3];
+            const real* mp = s_mu[(cu + 1) & 3];
+            real mn[9];
+            mn[1] = m0[mc + 1]; mn[2] = mp[mc]; mn[3] = m0[mc - 1]; mn[4] = mm[mc];
+            mn[5] = mp[mc + 1]; mn[6] = mp[mc - 1]; mn[7] = mm[mc - 1]; mn[8] = mm[mc + 1];
+            mn[0] = m0[mc];
+            const real rho = s_rho[cu & 7][rc];
+            const bool wall = WALLS && (cu == 0 || cu == ny - 1);
+            if (wall) mirror_neighbours(mn, cu != 0);
+            const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
+            const real Fx = -rho * grad_x(mn) + ext_fx(rho);
+            const real Fy = -rho * ((mn[2] - mn[4]) * w1 + ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2) + ext_fy(rho);
+            if (wall) wall_fill(p1, cu != 0, real(-0.5) * Fx, real(-0.5) * Fy);
+            const real jx = (p1[1] - p1[3]) + (p1[5] - p1[6]) + (p1[8] - p1[7]);
+            const real jy = (p1[2] - p1[4]) + (p1[5] + p1[6]) - (p1[7] + p1[8]);
+            s_ux[cu & 3][uc] = (jx + real(0.5) * Fx) / rho;
+            s_uy[cu & 3][uc] = (jy + real(0.5) * Fy) / rho;
+        }
+        __syncthreads();
+        if (is_main && has_col && r >= y0 + 3) {
+            const int c = r - 3;
+            const real* mm = s_mu[(c - 1) & 3];
+            const real* m0 = s_mu[c & 3];
+            const real* mp = s_mu[(c + 1) & 3];
+            const real* rm = s_rho[(c - 1) & 7];
+            const real* r0 = s_rho[c & 7];
+            const real* rp = s_rho[(c + 1) & 7];
+            const real* xm_ = s_ux[(c - 1) & 3];
+            const real* x0_ = s_ux[c & 3];
+            const real* xp_ = s_ux[(c + 1) & 3];
+            const real* ym_ = s_uy[(c - 1) & 3];
+            const real* y0_ = s_uy[c & 3];
+            const real* yp_ = s_uy[(c + 1) & 3];
+            real mn[9], rn[9], un[9], vn[9];
+            mn[1] = m0[mc + 1]; mn[2] = mp[mc]; mn[3] = m0[mc - 1]; mn[4] = mm[mc];
+            mn[5] = mp[mc + 1]; mn[6] = mp[mc - 1]; mn[7] = mm[mc - 1]; mn[8] = mm[mc + 1];
+            rn[1] = r0[rc + 1]; rn[2] = rp[rc]; rn[3] = r0[rc - 1]; rn[4] = rm[rc];
+            rn[5] = rp[rc + 1]; rn[6] = rp[rc - 1]; rn[7] = rm[rc - 1]; rn[8] = rm[rc + 1];
+            un[1] = x0_[uc + 1]; un[2] = xp_[uc]; un[3] = x0_[uc - 1]; un[4] = xm_[uc];
+            un[5] = xp_[uc + 1]; un[6] = xp_[uc - 1]; un[7] = xm_[uc - 1]; un[8] = xm_[uc + 1];
+            vn[1] = y0_[uc + 1]; vn[2] = yp_[uc]; vn[3] = y0_[uc - 1]; vn[4] = ym_[uc];
+            vn[5] = yp_[uc + 1]; vn[6] = yp_[uc - 1]; vn[7] = ym_[uc - 1]; vn[8] = ym_[uc + 1];
+            const real rho_c = r0[rc];
+            mn[0] = m0[mc];
+            rn[0] = rho_c;
+            un[0] = x0_[uc];
+            vn[0] = y0_[uc];
+            if (WALLS && (c == 0 || c == ny - 1)) {
+                const bool top = c != 0;
+                mirror_neighbours(mn, top);
+                mirror_neighbours(rn, top);
+                // velocity beyond a no-slip wall: odd extension through u = 0 at the wall node
+                if (!top) {
+                    un[4] = -un[2]; un[7] = -un[6]; un[8] = -un[5];
+                    vn[4] = -vn[2]; vn[7] = -vn[6]; vn[8] = -vn[5];
+                } else {
+                    un[2] = -un[4]; un[5] = -un[8]; un[6] = -un[7];
+                    vn[2] = -vn[4]; vn[5] = -vn[8]; vn[6] = -vn[7];
+                }
+            }
+            const real pg = E.on ? E.rho_g * E.g * (real(c) - E.y_ref) : real(0);
+            fe_collide_iwb(p0, rho_c, mn, rn, un, vn, ext_fx(rho_c), ext_fy(rho_c), pg, P, E);
+            const long long o = (long long)c * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
+        }
+        if (has_col) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                p0[i] = p1[i];
+                p1[i] = p2[i];
+                p2[i] = p3[i];
+                p3[i] = nxt[i];
+            }
+        }
+    }
+}
+
+// f = f^eq of Eq. (20) at rest with p_g, stored as S_i(y) = f^eq_i(y + c_i) (rows beyond a
+// wall hold slots no step reads; the row is wrapped there).
+template <typename real, typename src_t>
+__global__ void init_iwb_kernel(const src_t* __restrict__ rho0, real* __restrict__ S, int nx, int ny,
+                                long long pitch, double pg_coef, double y_ref) {
+    const int cxs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int cys[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                         1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+    const long long n = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx), y = (int)(c / nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ys = (y + cys[i] + ny) % ny;
+            const double pg = pg_coef * ((double)ys - y_ref);
+            const double r = (double)rho0[shifted_cell(x, y, cxs[i], cys[i], nx, ny)];
+            S[i * pitch + c] = (real)(i == 0 ? r - (1.0 - w[0]) * 3.0 * pg : w[i] * 3.0 * pg);
+        }
     }
 }
 

@@ -111,6 +111,7 @@ def _lib():
             "lbm_set_density": ([vp, dp], ctypes.c_int),
             "lbm_set_drive": ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_longlong],
                               ctypes.c_int),
+            "lbm_set_gravity": ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
             "lbm_set_density_device": ([vp, vp], ctypes.c_int),
             "lbm_set_populations": ([vp, dp], ctypes.c_int),
             "lbm_get_populations": ([vp, dp], ctypes.c_int),
@@ -287,6 +288,10 @@ class Context:
     def set_drive(self, ax_lo: float, ax_hi: float, x_split: float, t_on: int):
         """Droplet-collision drive of Sec. 5.4 (lbm_set_drive)."""
         _check(_lib().lbm_set_drive(self.h, float(ax_lo), float(ax_hi), float(x_split), int(t_on)), "lbm_set_drive")
+
+    def set_gravity(self, g: float, rho_ref: float, y_ref: float = 0.0):
+        """Free-energy gravity of Eqs. (20)-(21) (lbm_set_gravity)."""
+        _check(_lib().lbm_set_gravity(self.h, float(g), float(rho_ref), float(y_ref)), "lbm_set_gravity")
 
     def step(self, n: int):
         _check(_lib().lbm_step(self.h, int(n)), "lbm_step")

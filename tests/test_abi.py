@@ -77,9 +77,14 @@ def test_argument_errors(lib):
         with pytest.raises(lib.LBMError) as e:
             lib.lbm_resolve_params(lib.lbm_params_default(0, **kw))
         assert e.value.code == lib.LBM_ERR_ARG
-    with pytest.raises(lib.LBMError) as e:
-        lib.lbm_resolve_params(lib.lbm_params_default(1, A=0.1))
+    with pytest.raises(lib.LBMError) as e:  # A belongs to the free-energy equilibrium
+        lib.lbm_resolve_params(lib.lbm_params_default(0, A=0.1))
     assert e.value.code == lib.LBM_ERR_UNSUPPORTED
+    with pytest.raises(lib.LBMError) as e:  # nu = c_s^2 (tau - 1/2 - A) <= 0
+        lib.lbm_resolve_params(lib.lbm_params_default(1, A=0.5, tau_nu=1.0))
+    assert e.value.code == lib.LBM_ERR_ARG
+    out, _ = lib.lbm_resolve_params(lib.lbm_params_default(1, A=0.2, tau_nu=1.0))
+    assert out.A == 0.2
     assert lib.lbm_strerror(lib.LBM_ERR_DIVERGED).startswith("simulation diverged")
     assert lib.lbm_workspace_bytes(0, 0, 5) == 0
     assert lib.lbm_workspace_bytes(1, 256, 4) > 2 * 9 * 256 * 4 * 8

@@ -1,0 +1,119 @@
+"""GPU parity of the full improved well-balanced free-energy model (Eqs. 20, 21, 23): the
+viscosity-tuning term A (strain rate of u at the neighbours) and gravity (p_g, -grad p_g,
+buoyancy), periodic and between walls, against the FP64 oracle; the shear-wave viscosity
+c_s^2 (tau_nu - 1/2 - A) on the GPU."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2403_11167_gb300 import inputs
+from helpers import gpu_context, max_rel, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+FE = 1
+F32, F64 = 0, 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def _compare(ctx, rp, th, rho0, steps, walls=False, g=0.0, rho_g=0.0, y_ref=0.0, tol=1e-11):
+    p = oracle_params(rp, th, walls=walls)
+    p.g, p.rho_g, p.y_ref = g, rho_g, y_ref
+    f_ref = O.run(FE, p, O.init_iwb(p, rho0), steps)
+    f = ctx.populations()
+    err = max_rel(f, f_ref)
+    assert err < tol, err
+    rho_ref, ux_ref, uy_ref, *_ = O.macro(FE, p, f_ref)
+    rho, ux, uy = ctx.fields()
+    umax = max(np.abs(ux_ref).max(), np.abs(uy_ref).max())
+    assert max_rel(rho, rho_ref) < 10 * tol
+    assert np.abs(ux - ux_ref).max() < 1e3 * tol * umax and np.abs(uy - uy_ref).max() < 1e3 * tol * umax
+    return err
+
+
+@pytest.mark.parametrize("shape,kind", [((37, 29), "random"), ((80, 64), "droplet"), ((130, 7), "random")])
+def test_fp64_A_periodic(shape, kind):
+    """A = 0.15 (tau_nu = 1, tau_e = 0.9), body force: every population after 30 steps."""
+    nx, ny = shape
+    ctx, rp, th = gpu_context(FE, F64, nx, ny, a=0.25, Tr=0.8, tau_nu=1.0, tau_e=0.9, A=0.15, body_fx=2e-5,
+                              body_fy=-1e-5)
+    rho0 = (inputs.random_field(nx, ny, th.rho_v * 3, th.rho_l * 0.6, seed=nx + ny) if kind == "random"
+            else inputs.droplet(nx, ny, 16.0, th.rho_v, th.rho_l))
+    ctx.set_density(rho0)
+    ctx.step(30)
+    _compare(ctx, rp, th, rho0, 30)
+
+
+@pytest.mark.parametrize("shape", [(70, 42), (8, 4)])
+def test_fp64_A_gravity_walls(shape):
+    """A = 0.1 with gravity between walls (g = 1e-5 along -y, rho_0 = rho_l, y_ref = ny/2) and a
+    body force along x on a sine-perturbed channel: every population after 40 steps."""
+    nx, ny = shape
+    ctx, rp, th = gpu_context(FE, F64, nx, ny, walls=True, a=0.25, Tr=0.8, tau_nu=1.0, tau_e=1.0, A=0.1,
+                              body_fx=1e-5)
+    ctx.set_gravity(1e-5, th.rho_l, ny / 2)
+    rho0 = inputs.plate_channel(nx, ny, th.rho_v, th.rho_l, amp=min(3.0, ny / 8))
+    ctx.set_density(rho0)
+    ctx.step(40)
+    _compare(ctx, rp, th, rho0, 40, walls=True, g=1e-5, rho_g=th.rho_l, y_ref=ny / 2)
+
+
+def test_fp64_weight_periodic_with_drive():
+    """Plain weight (rho_0 = 0) on a periodic droplet pair with the Sec. 5.4 drive switched on
+    at t = 5 (A = 0): 70 steps across the switch-on."""
+    nx, ny = 80, 40
+    ctx, rp, th = gpu_context(FE, F64, nx, ny, a=0.25, Tr=0.8, tau_nu=1.0)
+    ctx.set_gravity(2e-6, 0.0, 0.0)
+    rho0 = inputs.two_droplets(nx, ny, [(20, 20), (60, 20)], 10.0, th.rho_v, th.rho_l)
+    ctx.set_density(rho0)
+    ctx.set_drive(5e-4, -3e-4, 40, 5)
+    ctx.step(70)
+    p = oracle_params(rp, th)
+    p.g = 2e-6
+    p.drive_ax_lo, p.drive_ax_hi, p.drive_x_split = 5e-4, -3e-4, 40.0
+    f_ref = O.run_driven(FE, p, O.init_iwb(p, rho0), 70, t0=0, t_on=5)
+    assert max_rel(ctx.populations(), f_ref) < 1e-11
+
+
+def test_fp32_A_droplet():
+    """FP32, A = 0.15, droplet 203 x 61 (R = 20), 100 steps: densities within 1e-5."""
+    nx, ny = 203, 61
+    ctx, rp, th = gpu_context(FE, F32, nx, ny, a=0.25, Tr=0.8, tau_nu=1.0, tau_e=0.9, A=0.15)
+    rho0 = inputs.droplet(nx, ny, 20.0, th.rho_v, th.rho_l)
+    ctx.set_density(rho0)
+    ctx.step(100)
+    p = oracle_params(rp, th)
+    f_ref = O.run(FE, p, O.init(FE, rho0), 100)
+    err = max_rel(ctx.populations().sum(0), f_ref.sum(0))
+    print("fp32 A", err)
+    assert err < 1e-5
+
+
+@pytest.mark.parametrize("A,tau", [(0.2, 1.0), (-0.2, 0.9)])
+def test_shear_wave_viscosity_gpu(A, tau):
+    """FP64 shear wave (L = 64): decay rate nu k^2 with nu = c_s^2 (tau - 1/2 - A), within 0.5%."""
+    L, nx, U = 64, 4, 1e-4
+    ctx, rp, th = gpu_context(FE, F64, nx, L, a=0.25, Tr=0.8, tau_nu=tau, tau_e=1.0, A=A)
+    rho = th.rho_l
+    f = O.init(FE, np.full((L, nx), rho))
+    y = np.arange(L)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    f = f + (w * cx)[:, None, None] * 3.0 * rho * (U * np.sin(2 * np.pi * y / L))[None, :, None]
+    ctx.set_populations(f)
+    amps = []
+    for s in (200, 1000):
+        ctx.step(s)
+        _, ux, _ = ctx.fields()
+        amps.append(2.0 / L * np.sum(ux[:, 0] * np.sin(2 * np.pi * y / L)))
+    nu = -np.log(amps[1] / amps[0]) / ((2 * np.pi / L) ** 2 * 1000)
+    assert abs(nu / ((tau - 0.5 - A) / 3.0) - 1) < 5e-3, nu
