@@ -1,0 +1,142 @@
+"""The paper's parameter studies run as batched GPU jobs.
+
+* ``table1`` -- Table 1 (Sec. 5.1): vapour-density error of a planar interface against the
+  Maxwell rule for tau_nu in {0.55, 0.75, 1, 1.2}; the free-energy model (all other relaxation
+  times 1, A = 0) and the pseudopotential model with tau_q = 1 and tau_q = 1/1.99 (other
+  relaxation times 1).  Tr = 0.65, a = 0.5, kappa = 0.5, kappa^Li = 0 and kappa^P giving the
+  free-energy interface width.  Planar runs are one-row periodic lattices of Lx = 100 started
+  from a tanh slab (W0 = 5) at rest; the vapour density is the mean of the two cells that
+  straddle x = 0.  The pseudopotential lattices run as one batch; the free-energy lattices
+  (which the batch does not take) run on FP64 contexts.
+* ``fig5`` -- Fig. 5 (Sec. 5.2): vapour density of a pseudopotential droplet (R = 20) at
+  Tr = 0.6, a = 0.25, with the empirical parameters of Sec. 5.2 (epsilon = 1.9168,
+  kappa^P = 0.919) and kappa^Li varied, which varies the surface tension gamma; against the
+  thermodynamically consistent vapour density of a droplet with that gamma (``kelvin_2d``).
+  All droplets run as one batch.
+
+Everything here composes library calls (parameter resolution, batches, contexts,
+observables); the host-side Carnahan-Starling formulas below are only used to evaluate the
+consistent droplet densities.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import inputs
+from . import lbm as L
+
+TABLE1_TAU_NU = (0.55, 0.75, 1.0, 1.2)
+TABLE1_TAU_Q = (1.0, 1.0 / 1.99)
+TABLE1_COND = dict(a=0.5, Tr=0.65, kappa=0.5)
+FIG5_COND = dict(a=0.25, Tr=0.6, eps=1.9168, kappa_P=0.919, radius=20.0, size=120)
+
+
+def _resolve(p):
+    out, th = L.lbm_resolve_params(p)
+    return out, th
+
+
+def table1(steps: int = 60000, nx: int = 100) -> dict:
+    """Vapour-density errors (percent, signed: (rho_v - rho_v^Maxwell) / rho_v^Maxwell) keyed
+    ("FE", 1.0, tau_nu) and ("P", tau_q, tau_nu)."""
+    import torch
+
+    a, Tr, kappa = TABLE1_COND["a"], TABLE1_COND["Tr"], TABLE1_COND["kappa"]
+    # kappa^P of the free-energy width (width match only: kappa^Li stays 0)
+    matched, _ = _resolve(L.lbm_params_default(L.LBM_PSEUDOPOTENTIAL, a=a, Tr=Tr, match_kappa=kappa))
+    out = {}
+    specs, rhos, keys = [], [], []
+    th_pp = None
+    for tq in TABLE1_TAU_Q:
+        for tn in TABLE1_TAU_NU:
+            p = L.lbm_params_default(L.LBM_PSEUDOPOTENTIAL, precision=L.LBM_F32, a=a, Tr=Tr, tau_nu=tn, tau_e=1.0,
+                                     tau_zeta=1.0, tau_q=tq, kappa_P=matched.kappa_P, kappa_Li=0.0)
+            _, th_pp = _resolve(p)
+            specs.append(dict(nx=nx, ny=1, geometry=0, nsteps=steps, params=p))
+            rhos.append(inputs.flat_slab(nx, 1, th_pp.rho_v, th_pp.rho_l))
+            keys.append(("P", tq, tn))
+    b = L.Batch(specs, rhos)
+    b.run()
+    for k, o in zip(keys, b.observables()):
+        out[k] = 100.0 * (o["rho_v"] - th_pp.rho_v) / th_pp.rho_v
+    b.close()
+    for tn in TABLE1_TAU_NU:
+        p = L.lbm_params_default(L.LBM_FREE_ENERGY, precision=L.LBM_F64, a=a, Tr=Tr, tau_nu=tn, tau_e=1.0,
+                                 tau_zeta=1.0, tau_q=1.0, kappa=kappa)
+        ctx = L.Context(p, nx, 1)
+        _, th = ctx.derived()
+        ctx.set_density(inputs.flat_slab(nx, 1, th.rho_v, th.rho_l))
+        ctx.step(steps)
+        o = ctx.observables(L.FLAT)
+        out[("FE", 1.0, tn)] = 100.0 * (o["rho_v"] - th.rho_v) / th.rho_v
+        ctx.close()
+    torch.cuda.synchronize()
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# Carnahan-Starling pressure and chemical potential (Eqs. 28, 29) on the host, for the
+# consistent densities of a droplet.
+
+def _p_cs(rho, a, b, R, T):
+    e = b * rho / 4.0
+    return rho * R * T * (1 + e + e * e - e ** 3) / (1 - e) ** 3 - a * rho * rho
+
+
+def _mu_cs(rho, a, b, R, T):
+    e = b * rho / 4.0
+    return R * T * (3.0 - e) / (1.0 - e) ** 3 + R * T * math.log(rho) + R * T - 2.0 * a * rho
+
+
+def _dp(rho, a, b, R, T, h=1e-7):
+    return (_p_cs(rho + h, a, b, R, T) - _p_cs(rho - h, a, b, R, T)) / (2 * h)
+
+
+def kelvin_2d(a: float, b: float, R: float, T: float, gamma: float, radius: float, rho_v0: float,
+              rho_l0: float) -> tuple[float, float]:
+    """Thermodynamically consistent densities of a 2-D droplet of the given radius and surface
+    tension: equal chemical potential in both phases and p(rho_l) - p(rho_v) = gamma / radius
+    (Laplace), by Newton's method from the planar (Maxwell) pair (rho_v0, rho_l0)."""
+    rv, rl = rho_v0, rho_l0
+    for _ in range(50):
+        f1 = _mu_cs(rl, a, b, R, T) - _mu_cs(rv, a, b, R, T)
+        f2 = _p_cs(rl, a, b, R, T) - _p_cs(rv, a, b, R, T) - gamma / radius
+        # d mu / d rho = (dp/drho) / rho
+        j11, j12 = -_dp(rv, a, b, R, T) / rv, _dp(rl, a, b, R, T) / rl
+        j21, j22 = -_dp(rv, a, b, R, T), _dp(rl, a, b, R, T)
+        det = j11 * j22 - j12 * j21
+        drv = (-f1 * j22 + f2 * j12) / det
+        drl = (-j11 * f2 + j21 * f1) / det
+        rv, rl = rv + drv, rl + drl
+        if abs(drv) < 1e-15 * rv and abs(drl) < 1e-15 * rl:
+            break
+    return rv, rl
+
+
+def fig5(kappa_li_values=(-3.0, -2.4, -1.7, -1.2, -0.6, 0.0), steps: int = 20000) -> list:
+    """Per kappa^Li: surface tension gamma of the model (planar theory), the measured droplet
+    vapour density, the consistent one (kelvin_2d at the measured equimolar radius), both
+    reduced by rho_c, and the relative error."""
+    c = FIG5_COND
+    specs, rhos, ths = [], [], []
+    for kli in kappa_li_values:
+        p = L.lbm_params_default(L.LBM_PSEUDOPOTENTIAL, precision=L.LBM_F32, a=c["a"], Tr=c["Tr"], tau_nu=1.0,
+                                 tau_e=1.0, tau_zeta=1.0, tau_q=1.0 / 1.99, kappa_P=c["kappa_P"], kappa_Li=kli,
+                                 sigma_Li=c["eps"] / 16.0)
+        _, th = _resolve(p)
+        ths.append(th)
+        n = c["size"]
+        specs.append(dict(nx=n, ny=n, geometry=1, nsteps=steps, params=p))
+        rhos.append(inputs.droplet(n, n, c["radius"], th.rho_v, th.rho_l))
+    b = L.Batch(specs, rhos)
+    b.run()
+    rows = []
+    for kli, th, o in zip(kappa_li_values, ths, b.observables()):
+        rv_c, _ = kelvin_2d(c["a"], 4.0, 1.0, th.T, th.gamma, o["radius"], th.rho_v, th.rho_l)
+        rows.append(dict(kappa_li=kli, gamma=th.gamma, radius=o["radius"], rho_v=o["rho_v"] / th.rho_c,
+                         rho_v_consistent=rv_c / th.rho_c, rel_err=o["rho_v"] / rv_c - 1.0,
+                         status=o["status"]))
+    b.close()
+    return rows
