@@ -453,10 +453,13 @@ __device__ __forceinline__ void pp_collide(float v[9], float rho, float pc, cons
 // serve FP64).
 __device__ __forceinline__ void fe_collide(float v[9], float rho, const float mn[9], const float rn[9],
                                            const StepParams<float>& P) {
+    // entry 0 of mn, rn (the cell itself) is not used and callers need not set it
     F1 vv[9], m[9], r[9];
+    m[0] = r[0] = F1(0.0f);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        vv[i] = F1(v[i]);
+    for (int i = 0; i < 9; ++i) vv[i] = F1(v[i]);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
         m[i] = F1(mn[i]);
         r[i] = F1(rn[i]);
     }
@@ -465,9 +468,11 @@ __device__ __forceinline__ void fe_collide(float v[9], float rho, const float mn
     for (int i = 0; i < 9; ++i) v[i] = vv[i].v;
 }
 __device__ __forceinline__ float fe_mu(float rc, const float rn[9], const StepParams<float>& P) {
+    // rn[0] is not used and callers need not set it
     F1 r[9];
+    r[0] = F1(rc);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) r[i] = F1(rn[i]);
+    for (int i = 1; i < 9; ++i) r[i] = F1(rn[i]);
     return fe_mu_v(F1(rc), r, P).v;
 }
 
