@@ -17,6 +17,7 @@ def main():
     ap.add_argument("--model", choices=["pp", "fe"], default="pp")
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--A", type=float, default=0.0, help="free-energy A != 0 runs the full-model kernel")
     args = ap.parse_args()
     import torch
 
@@ -24,7 +25,7 @@ def main():
 
     build.build()
     model = lbm.LBM_PSEUDOPOTENTIAL if args.model == "pp" else lbm.LBM_FREE_ENERGY
-    p = lbm.lbm_params_default(model, precision=lbm.LBM_F32, a=0.25, Tr=0.85, tau_nu=0.8)
+    p = lbm.lbm_params_default(model, precision=lbm.LBM_F32, a=0.25, Tr=0.85, tau_nu=0.8, A=args.A)
     ctx = lbm.Context(p, args.size, args.size)
     _, th = ctx.derived()
     ctx.set_density(inputs.spinodal_noise(args.size, args.size, 0.5 * (th.rho_l + th.rho_v), 0.01, seed=2403))
