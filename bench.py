@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned calibration surrogate")
     ap.add_argument("--surrogate-sets", type=int, default=8000)
     ap.add_argument("--no-walls", action="store_true", help="skip the walled-channel measurement")
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="reference arm: seconds of oracle work per timed step (default: ~1 min in total)")
     ap.add_argument("--plain-sets", type=int, default=6, help="held-out sets also calibrated one lattice at a time")
     return ap.parse_args()
 
@@ -132,7 +134,7 @@ def run_reference(args):
     if rank != 0:
         return
     rho0 = make_rho0(args.size)
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = args.ref_seconds or max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_mlups(rho0, per_step / 4)
     vals, cores, sample = [], 1, ""

@@ -61,3 +61,30 @@ def test_single_rank_needs_no_process_group():
 
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.job_rate(10.0, 1, 2.0) == 5.0
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores and prints one JSON
+    line with the GPU arm's metric, unit and config, impl = reference, a cpu_baseline of kind
+    oracle and an e2e object without host-device copies (no GPU needed)."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--ref-seconds", "0.3"], capture_output=True, text=True, timeout=600,
+                         cwd=root, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "MLUPS"
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("spinodal decomposition, 4096x4096")
