@@ -66,7 +66,9 @@ typedef struct {
     double kappa_P, kappa_Li, sigma_Li; /* MP-LBM, Eqs. (30)-(32) */
     double kappa;       /* FE-LBM surface-tension parameter, mu = mu_b - kappa lap rho */
     double fx, fy;      /* constant body force added to the total force */
-    double walls;       /* 0: periodic in y; 1: no-slip walls on rows 0 and ny-1 (Sec. 5.3) */
+    double walls;       /* 0: periodic in y; 1: no-slip walls on rows 0 and ny-1 (Sec. 5.3);
+                           2: the same walls with the free-energy wall rows' normal mu
+                           gradient one-sided (see fe_wall_density) */
     double drive;       /* 1: add the droplet-collision force of Sec. 5.4 (drive_force) */
     double drive_ax_lo, drive_ax_hi, drive_x_split;
     double A;           /* FE viscosity-tuning term of Eqs. (20), (23) */
@@ -479,6 +481,56 @@ static void stencil_grad_vel(const double* phi, int nx, int ny, int walls, int x
     *gy = sy / CS2;
 }
 
+/* Free-energy walls = 2: at a wall row the normal component of grad mu is taken one-sided,
+ * through the ghost mu(-1) = 2 mu(0) - mu(1) (bottom; mirrored at the top), instead of through
+ * the mirrored row (which makes it zero).  With a wall-normal force (fy, gravity) the mirrored
+ * reading leaves the wall node's force unbalanced at hydrostatic equilibrium, and the free-energy
+ * model's neutral period-2 density mode, which no central-difference stencil damps, grows from
+ * the wall rows without bound; the one-sided gradient removes that source.  The wall node's
+ * density then depends on its own normal force (sum_i f_i = K +- J_y, J_y = -F_y/2, F_y through
+ * mu(0), mu(1)), so it is found by fixed-point iteration of fill and force. */
+static double fe_wall_grad_y(const double* mu, int nx, int ny, int x, int y) {
+    const int yi = y == 0 ? 1 : ny - 2;
+    const double sgn = y == 0 ? 1.0 : -1.0;
+    double s = 0.0;
+    for (int dx = -1; dx <= 1; ++dx) {
+        const double w = dx == 0 ? WI[2] : WI[5];  /* axis and diagonal weights */
+        const int xx = wrap(x + dx, nx);
+        s += w * 2.0 * (mu[yi * nx + xx] - mu[y * nx + xx]);
+    }
+    return sgn * s / CS2;
+}
+
+static void fe_wall_density(const orc_params* p, int nx, int ny, double* f, double* rho, double* mu,
+                            double* Fy) {
+    size_t N = (size_t)nx * ny;
+    for (int it = 0; it < 200; ++it) {
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                mu[(size_t)y * nx + x] = mu_bulk(p, rho[(size_t)y * nx + x]) - p->kappa * stencil_lap(rho, nx, ny, 1, x, y);
+        for (int side = 0; side < 2; ++side) {
+            const int y = side == 0 ? 0 : ny - 1;
+            for (int x = 0; x < nx; ++x) {
+                size_t c = (size_t)y * nx + x;
+                Fy[c] = -rho[c] * fe_wall_grad_y(mu, nx, ny, x, y) + p->fy - (rho[c] - p->rho_g) * p->g;
+            }
+        }
+        wall_fill(p, nx, ny, f, NULL, Fy);
+        double dmax = 0.0;
+        for (int side = 0; side < 2; ++side) {
+            const int y = side == 0 ? 0 : ny - 1;
+            for (int x = 0; x < nx; ++x) {
+                size_t c = (size_t)y * nx + x;
+                double s = 0.0;
+                for (int i = 0; i < Q9; ++i) s += f[(size_t)i * N + c];
+                dmax = fmax(dmax, fabs(s - rho[c]));
+                rho[c] = s;
+            }
+        }
+        if (dmax <= 1e-16 * rho[0]) break;
+    }
+}
+
 /* Density, chemical potential, gradients, force and velocity of the FE model. */
 static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho,
                      double* mu, double* Fx, double* Fy, double* ux, double* uy, double* drx,
@@ -494,7 +546,8 @@ static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho
         if (!(s > 0.0) || !(p->b * s / 4.0 < 1.0)) bad = 1;
     }
     if (bad) return -1;
-    if (p->walls != 0.0 && p->g != 0.0) {
+    if (p->walls == 2.0) fe_wall_density(p, nx, ny, f, rho, mu, Fy);
+    if (p->walls == 1.0 && p->g != 0.0) {
         /* a wall node's normal force includes gravity, -(rho - rho_0) g, which depends on its
          * own density: sum_i f_i = K + Jy (bottom) or K - Jy (top), Jy = -F_y/2, solved for
          * rho in closed form from the first fill's density (Jy = -fy/2) and filled again */
@@ -535,8 +588,9 @@ static int fe_fields(const orc_params* p, int nx, int ny, double* f, double* rho
             const double Fg = -(rho[c] - p->rho_g) * p->g;  /* buoyancy F_g of Eq. (21) */
             Fx[c] = -rho[c] * gmx + p->fx + drive_force(p, x, rho[c], rave);
             Fy[c] = -rho[c] * gmy + p->fy + Fg;
-            if (is_wall_row(p, y, ny)) {  /* mirrored neighbours: no normal gradient */
-                Fy[c] = p->fy + Fg;
+            if (is_wall_row(p, y, ny)) {
+                /* walls = 1: mirrored neighbours, no normal gradient; walls = 2: one-sided */
+                Fy[c] = p->walls == 2.0 ? -rho[c] * fe_wall_grad_y(mu, nx, ny, x, y) + p->fy + Fg : p->fy + Fg;
                 dry[c] = 0.0;
             }
         }

@@ -85,3 +85,28 @@ def test_gravity_and_A_off_reproduce_the_plain_model():
     f1 = O.run(O.FE, p, O.init(O.FE, rho0), 30)
     f2 = O.run(O.FE, p, O.init_iwb(p, rho0), 30)
     assert np.array_equal(f1, f2)
+
+
+@pytest.mark.parametrize("force", ["fy", "gravity"])
+def test_wall_normal_force_period2_mode(force):
+    """A liquid column between walls under a wall-normal force (body force fy = -1e-5, or
+    gravity g = 1e-5 with rho_0 = rho_l): with mirrored wall rows (walls = 1) the free-energy
+    model's neutral period-2 density mode grows from the walls without bound (the second
+    differences of rho keep growing: x3 between 8e3 and 2e4 steps); with the one-sided normal mu
+    gradient and a self-consistent wall density (walls = 2) the column is steady (second
+    differences below 1e-5 and unchanged, velocity ~ 0)."""
+    rv, rl, _ = thermo.maxwell(A_EOS, 4.0, 1.0, 0.8)
+    ny, nx = 40, 4
+    kw = dict(fy=-1e-5) if force == "fy" else dict(g=1e-5, rho_g=rl)
+    amp = {}
+    for walls in (1.0, 2.0):
+        p = O.make_params(a=A_EOS, b=4.0, R=1.0, T=_T(), tau_nu=1.0, tau_e=1.0, kappa=0.5, walls=walls, **kw)
+        f = O.init_iwb(p, np.full((ny, nx), rl))
+        f8 = O.run(O.FE, p, f, 8000)
+        f20 = O.run(O.FE, p, f8, 12000)
+        a8 = np.abs(np.diff(O.macro(O.FE, p, f8)[0][4:-4, 0], 2)).max()
+        rho, ux, uy, *_ = O.macro(O.FE, p, f20)
+        amp[walls] = (a8, np.abs(np.diff(rho[4:-4, 0], 2)).max(), np.abs(uy).max())
+    grow1, grow2 = amp[1.0][1] / amp[1.0][0], amp[2.0][1] / amp[2.0][0]
+    assert grow1 > 2.0 and amp[1.0][1] > 1e-3
+    assert amp[2.0][1] < 1e-5 and abs(grow2 - 1) < 0.05 and amp[2.0][2] < 1e-7
