@@ -52,7 +52,7 @@ extern "C" {
 #define LBM_ERR_IO (-8)           /* checkpoint file could not be read or written */
 
 typedef enum { LBM_PSEUDOPOTENTIAL = 0, LBM_FREE_ENERGY = 1 } lbm_model;
-typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL_ZOUHE = 1 } lbm_bc;
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL_ZOUHE = 1, LBM_BC_WALL_ZOUHE_ONESIDED = 2 } lbm_bc;
 typedef enum { LBM_F32 = 0, LBM_F64 = 1 } lbm_precision;
 typedef enum { LBM_GEOMETRY_FLAT = 0, LBM_GEOMETRY_DROPLET = 1 } lbm_geometry;
 
@@ -138,8 +138,14 @@ size_t lbm_workspace_bytes(int precision, int nx, int ny);
  * node rows 0 and ny-1 (needs ny >= 4), the parallel-plate channel of Sec. 5.3: Zou and
  * He's condition completes a wall node's incoming populations so that its momentum is
  * -F/2 (u = 0 including the half-force shift of Eq. 6b), and every stencil sees beyond
- * a wall the row mirrored through it.  The body force body_fx/fy drives the flow.  Any
- * other bc returns LBM_ERR_UNSUPPORTED.  stream: a cudaStream_t to run on, or
+ * a wall the row mirrored through it.  The body force body_fx/fy drives the flow.
+ * LBM_BC_WALL_ZOUHE_ONESIDED: the same walls, but the free-energy model takes the wall rows'
+ * normal chemical-potential gradient one-sided (ghost mu(-1) = 2 mu(0) - mu(1)) and solves the
+ * wall rows' densities self-consistently each step (the normal force then depends on them);
+ * with a wall-normal force (body_fy, gravity) the mirrored reading drives the free-energy
+ * model's neutral period-2 density mode from the walls, this one does not.  For the
+ * pseudopotential model it equals LBM_BC_WALL_ZOUHE.  Any other bc returns
+ * LBM_ERR_UNSUPPORTED.  stream: a cudaStream_t to run on, or
  * NULL for a stream the context creates and owns.  workspace: NULL to let the
  * library cudaMalloc its memory, or a device pointer (256-byte aligned) of at least
  * lbm_workspace_bytes(...) bytes that stays owned by the caller and must outlive

@@ -106,6 +106,8 @@ struct lbm_ctx {
     int* d_err;          // device error word of the TMA kernels (bounded waits)
     bool use_tma;
     bool walls;          // no-slip walls on rows 0 and ny-1 (direct wall kernels)
+    bool onesided;       // free-energy walls with the one-sided normal mu gradient (LBM_BC_WALL_ZOUHE_ONESIDED)
+    void* wall;          // 14 nx reals: the wall rows' J_y and solve scratch (fe_wall_solve_kernel)
     bool drive;          // droplet-collision drive configured (lbm_set_drive)
     bool grav;           // gravity configured (lbm_set_gravity; free-energy model)
     double g, rho_g, y_ref;
@@ -320,7 +322,9 @@ extern "C" size_t lbm_workspace_bytes(int precision, int nx, int ny) {
     const size_t n = (size_t)nx * ny;
     const size_t fbytes = align256(9 * (size_t)plane_pitch(nx, ny) * esz);
     const size_t fields = align256(4 * n * esz);
-    return 2 * fbytes + fields + align256(kRedBlocks * 3 * sizeof(double)) + align256(8 * sizeof(double)) + 256;
+    // ... + the one-sided walls' row solve (14 nx reals)
+    return 2 * fbytes + fields + align256(kRedBlocks * 3 * sizeof(double)) + align256(8 * sizeof(double)) + 256 +
+           align256(14 * (size_t)nx * esz);
 }
 
 template <typename real>
@@ -386,8 +390,10 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
     if (!p || nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31)) return LBM_ERR_ARG;
-    if (bc_x != LBM_BC_PERIODIC || (bc_y != LBM_BC_PERIODIC && bc_y != LBM_BC_WALL_ZOUHE)) return LBM_ERR_UNSUPPORTED;
-    const bool walls = bc_y == LBM_BC_WALL_ZOUHE;
+    if (bc_x != LBM_BC_PERIODIC ||
+        (bc_y != LBM_BC_PERIODIC && bc_y != LBM_BC_WALL_ZOUHE && bc_y != LBM_BC_WALL_ZOUHE_ONESIDED))
+        return LBM_ERR_UNSUPPORTED;
+    const bool walls = bc_y == LBM_BC_WALL_ZOUHE || bc_y == LBM_BC_WALL_ZOUHE_ONESIDED;
     if (walls && ny < 4) return LBM_ERR_ARG;
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ERR_ARG;
@@ -434,7 +440,9 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->partials = reinterpret_cast<double*>(c->ws + 2 * fbytes + align256(4 * n * c->esz));
     c->d_obs = reinterpret_cast<double*>(reinterpret_cast<char*>(c->partials) + align256(kRedBlocks * 3 * sizeof(double)));
     c->d_err = reinterpret_cast<int*>(reinterpret_cast<char*>(c->d_obs) + align256(8 * sizeof(double)));
+    c->wall = reinterpret_cast<char*>(c->d_err) + 256;
     c->walls = walls;
+    c->onesided = bc_y == LBM_BC_WALL_ZOUHE_ONESIDED && p->model == LBM_FREE_ENERGY;
     // walls: the periodic strip kernels serve the interior when both wall bands fit
     c->use_tma = (!walls || (kPPPair && kFEPair && ny >= 2 * kWallBandFE)) && c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 4 && std::getenv("LBM_NO_TMA") == nullptr;
     cudaError_t e = cudaMallocHost(&c->h_pinned, 8 * sizeof(double));
@@ -544,6 +552,13 @@ static lbmk::Drive<real> launch_drive(lbm_ctx* c, int src) {
     return d;
 }
 
+constexpr int kWallIters = 40;  // Jacobi sweeps of the one-sided walls' density solve
+
+// One-sided free-energy walls: solve the wall rows' J_y for the state in buffer src; returns
+// the J_y array the step and field kernels read (nullptr when the walls are mirrored).
+template <typename real>
+static const real* launch_wall_solve(lbm_ctx* c, int src, const lbmk::StepParams<real>& sp);
+
 // One step with the droplet-collision drive acting (periodic lattice, direct kernels).
 static int launch_step_driven(lbm_ctx* c, int src) {
     const void* fin = c->f[src];
@@ -557,7 +572,7 @@ static int launch_step_driven(lbm_ctx* c, int src) {
                 <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, d);
         else
             lbmk::fe_step_ext<float, kTXf, false>
-                <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, d);
+                <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, d, nullptr);
     } else {
         const lbmk::Drive<double> d = launch_drive<double>(c, src);
         dim3 grid((c->nx + kTXd - 1) / kTXd, (c->ny + c->rows - 1) / c->rows);
@@ -566,7 +581,7 @@ static int launch_step_driven(lbm_ctx* c, int src) {
                 <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, d);
         else
             lbmk::fe_step_ext<double, kTXd, false>
-                <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, d);
+                <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, d, nullptr);
     }
     CK(cudaGetLastError());
     return LBM_OK;
@@ -594,10 +609,22 @@ static void launch_iwb(lbm_ctx* c, int src, bool driven, const lbmk::StepParams<
     dim3 grid((c->nx + TX - 1) / TX, (c->ny + c->rows - 1) / c->rows);
     const real* fin = static_cast<const real*>(c->f[src]);
     real* fout = static_cast<real*>(c->f[src ^ 1]);
+    const real* wjy = launch_wall_solve<real>(c, src, sp);
     if (c->walls)
-        lbmk::fe_step_iwb<real, TX, true><<<grid, TX + 32, 0, c->stream>>>(fin, fout, sp, d, ext_terms<real>(c));
+        lbmk::fe_step_iwb<real, TX, true>
+            <<<grid, TX + 32, 0, c->stream>>>(fin, fout, sp, d, ext_terms<real>(c), wjy);
     else
-        lbmk::fe_step_iwb<real, TX, false><<<grid, TX + 32, 0, c->stream>>>(fin, fout, sp, d, ext_terms<real>(c));
+        lbmk::fe_step_iwb<real, TX, false>
+            <<<grid, TX + 32, 0, c->stream>>>(fin, fout, sp, d, ext_terms<real>(c), nullptr);
+}
+
+template <typename real>
+static const real* launch_wall_solve(lbm_ctx* c, int src, const lbmk::StepParams<real>& sp) {
+    if (!c->onesided) return nullptr;
+    real* w = static_cast<real*>(c->wall);
+    lbmk::fe_wall_solve_kernel<real>
+        <<<2, 256, 0, c->stream>>>(static_cast<const real*>(c->f[src]), sp, ext_terms<real>(c), w, kWallIters);
+    return w;
 }
 
 static int launch_step(lbm_ctx* c, int src, bool driven = false) {
@@ -624,10 +651,11 @@ static int launch_step(lbm_ctx* c, int src, bool driven = false) {
                 (const float*)fin, (float*)fout, c->spf, band, no_drive<float>());
         } else {
             dim3 grid((c->nx + kFEPTX - 1) / kFEPTX, (c->ny + c->rows - 1) / c->rows);
+            const float* wjy = launch_wall_solve<float>(c, src, c->spf);
             lbmk::fe_step_pair<kFEPWarps, kFEPStages><<<grid, (kFEPWarps + 1) * 32, sizeof(FEPSmem), c->stream>>>(
                 (const float*)fin, (float*)fout, c->spf, c->d_err);
             lbmk::fe_step_ext<float, kTXf, true><<<dim3((c->nx + kTXf - 1) / kTXf, 2), kTXf + 32, 0, c->stream>>>(
-                (const float*)fin, (float*)fout, c->spf, band, no_drive<float>());
+                (const float*)fin, (float*)fout, c->spf, band, no_drive<float>(), wjy);
         }
     } else if (c->walls) {
         if (c->prec == LBM_F32) {
@@ -636,16 +664,17 @@ static int launch_step(lbm_ctx* c, int src, bool driven = false) {
                 lbmk::pp_step_ext<float, kTXf, true>
                     <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, no_drive<float>());
             else
-                lbmk::fe_step_ext<float, kTXf, true>
-                    <<<grid, kTXf + 32, 0, c->stream>>>((const float*)fin, (float*)fout, c->spf, 0, no_drive<float>());
+                lbmk::fe_step_ext<float, kTXf, true><<<grid, kTXf + 32, 0, c->stream>>>(
+                    (const float*)fin, (float*)fout, c->spf, 0, no_drive<float>(), launch_wall_solve<float>(c, src, c->spf));
         } else {
             dim3 grid((c->nx + kTXd - 1) / kTXd, (c->ny + c->rows - 1) / c->rows);
             if (pp)
                 lbmk::pp_step_ext<double, kTXd, true>
                     <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, no_drive<double>());
             else
-                lbmk::fe_step_ext<double, kTXd, true>
-                    <<<grid, kTXd + 32, 0, c->stream>>>((const double*)fin, (double*)fout, c->spd, 0, no_drive<double>());
+                lbmk::fe_step_ext<double, kTXd, true><<<grid, kTXd + 32, 0, c->stream>>>(
+                    (const double*)fin, (double*)fout, c->spd, 0, no_drive<double>(),
+                    launch_wall_solve<double>(c, src, c->spd));
         }
     } else if (c->use_tma && pp && kPPPair) {
         dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
@@ -935,17 +964,19 @@ static int compute_fields(lbm_ctx* c, const lbmk::StepParams<real>& sp) {
         real* fw = static_cast<real*>(c->f[c->cur]);
         const lbmk::Ext<real> ex = ext_terms<real>(c);
         if (c->walls) {
-            lbmk::rho_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, sp, model, ex);
+            const real* wjy = launch_wall_solve<real>(c, c->cur, sp);
+            lbmk::rho_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, sp, model, ex, wjy);
             if (model == LBM_FREE_ENERGY) lbmk::mu_walls_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
             lbmk::walls_complete_kernel<real>
-                <<<(2 * c->nx + 255) / 256, 256, 0, c->stream>>>(fw, rho, aux, sp, model, ex);
+                <<<(2 * c->nx + 255) / 256, 256, 0, c->stream>>>(fw, rho, aux, sp, model, ex, c->onesided ? 1 : 0);
         } else {
             lbmk::rho_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(f, rho, aux, sp, model);
             if (model == LBM_FREE_ENERGY) lbmk::mu_kernel<real><<<kRedBlocks, 256, 0, c->stream>>>(rho, aux, sp);
         }
         const lbmk::Drive<real> d = driven_at(c, c->step) ? launch_drive<real>(c, c->cur) : no_drive<real>();
         lbmk::velocity_ext_kernel<real>
-            <<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, ux, uy, sp, model, c->walls ? 1 : 0, d, ex);
+            <<<kRedBlocks, 256, 0, c->stream>>>(fw, rho, aux, ux, uy, sp, model, c->walls ? 1 : 0, d, ex,
+                                                c->onesided ? 1 : 0);
         CK(cudaGetLastError());
         return LBM_OK;
     }

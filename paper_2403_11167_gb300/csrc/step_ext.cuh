@@ -107,12 +107,26 @@ __device__ __forceinline__ int stencil_row(int y, int ny) {
 // row: in bounds, and overwritten by the fill.
 template <bool WALLS, typename real>
 __device__ __forceinline__ void pull_row_ext(const real* __restrict__ f, const StepParams<real>& P, int x, int xm,
-                                             int xp, int y, real v[9]) {
+                                             int xp, int y, real v[9], const real* __restrict__ wjy = nullptr) {
     const int ny = P.ny, nx = P.nx;
     const long long om = (long long)(y == 0 ? ny - 1 : y - 1) * nx, o0 = (long long)y * nx,
                     op = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
     pull9(f, P.pitch, x, xm, xp, om, o0, op, v);
-    if (WALLS && (y == 0 || y == ny - 1)) wall_fill(v, y != 0, real(0), real(-0.5) * P.fy);
+    // wjy: the wall rows' solved J_y (one-sided reading, fe_wall_solve_kernel), bottom then top
+    if (WALLS && (y == 0 || y == ny - 1))
+        wall_fill(v, y != 0, real(0), wjy ? wjy[(y != 0 ? nx : 0) + x] : real(-0.5) * P.fy);
+}
+
+// One-sided reading of the free-energy walls: the wall-normal Eq. (24) gradient of mu at a
+// wall node through the ghost mu(-1) = 2 mu(0) - mu(1) (bottom; mu(ny) = 2 mu(ny-1) - mu(ny-2)
+// at the top), n[i] = mu at x + c_i (only the entries inside the lattice are read).  With the
+// mirrored reading a wall-normal force (fy, gravity) is left unbalanced at the wall node and
+// drives the free-energy model's neutral period-2 mode; this reading removes that source.
+template <typename real>
+__device__ __forceinline__ real wall_grad_y_onesided(const real n[9], bool top) {
+    const real a = real(2.0 / 9.0), d = real(1.0 / 18.0);
+    if (!top) return real(3) * (a * (n[2] - n[0]) + d * ((n[5] - n[1]) + (n[6] - n[3])));
+    return -real(3) * (a * (n[4] - n[0]) + d * ((n[8] - n[1]) + (n[7] - n[3])));
 }
 
 // Droplet-collision drive; rho_ave == nullptr: none.
@@ -287,7 +301,8 @@ __global__ void __launch_bounds__(TX + 32) pp_step_ext(const real* __restrict__ 
 // rho (8 rows, 2 halo columns each side), mu (4 rows, 1 halo column).
 template <typename real, int TX, bool WALLS>
 __global__ void __launch_bounds__(TX + 32) fe_step_ext(const real* __restrict__ fin, real* __restrict__ fout,
-                                                       const StepParams<real> P, int band, const Drive<real> D) {
+                                                       const StepParams<real> P, int band, const Drive<real> D,
+                                                       const real* __restrict__ wjy) {
     __shared__ real s_rho[8][TX + 4];
     __shared__ real s_mu[4][TX + 2];
     const real s_rave = D.rho_ave ? real(*D.rho_ave) : real(0);
@@ -319,11 +334,11 @@ __global__ void __launch_bounds__(TX + 32) fe_step_ext(const real* __restrict__ 
     const int xm = x == 0 ? nx - 1 : x - 1;
     const int xp = x == nx - 1 ? 0 : x + 1;
     real p0[9], p1[9], p2[9];  // pulled populations of rows r-2, r-1, r
-    if (has_col) pull_row_ext<WALLS>(fin, P, x, xm, xp, stencil_row<WALLS>(y0 - 2, ny), p2);
+    if (has_col) pull_row_ext<WALLS>(fin, P, x, xm, xp, stencil_row<WALLS>(y0 - 2, ny), p2, wjy);
 #pragma unroll 1
     for (int r = y0 - 2; r <= y1 + 1; ++r) {
         real nxt[9];
-        if (has_col && r <= y1) pull_row_ext<WALLS>(fin, P, x, xm, xp, stencil_row<WALLS>(r + 1, ny), nxt);
+        if (has_col && r <= y1) pull_row_ext<WALLS>(fin, P, x, xm, xp, stencil_row<WALLS>(r + 1, ny), nxt, wjy);
         if (has_col) s_rho[r & 7][rc] = sum9(p2);
         __syncthreads();
         if (has_mu && r >= y0) {
@@ -361,18 +376,22 @@ __global__ void __launch_bounds__(TX + 32) fe_step_ext(const real* __restrict__ 
             const real rho_c = r0[rc];
             mn[0] = m0[mc];
             rn[0] = rho_c;
+            StepParams<real> Pc = P;
             if (WALLS && (c == 0 || c == ny - 1)) {
+                // one-sided reading: the normal force -rho d_y mu enters through fy (the
+                // mirrored mu below makes the collision's own normal gradient zero)
+                if (wjy) Pc.fy = P.fy - rho_c * wall_grad_y_onesided(mn, c != 0);
                 // mu beyond the wall is mu of the mirrored row (the ring holds the value
                 // recomputed from mirrored rho, equal up to rounding order)
                 mirror_neighbours(mn, c != 0);
                 mirror_neighbours(rn, c != 0);
                 const real Fx = -rho_c * grad_x(mn) + P.fx;  // F = -rho grad mu + body force
-                wall_fill(p0, c != 0, real(-0.5) * Fx, real(-0.5) * P.fy);
+                wall_fill(p0, c != 0, real(-0.5) * Fx, real(-0.5) * Pc.fy);
             }
             if (D.rho_ave)
-                fe_collide(p0, rho_c, mn, rn, with_drive(P, D, x, rho_c, s_rave));
+                fe_collide(p0, rho_c, mn, rn, with_drive(Pc, D, x, rho_c, s_rave));
             else
-                fe_collide(p0, rho_c, mn, rn, P);
+                fe_collide(p0, rho_c, mn, rn, Pc);
             const long long o = (long long)c * nx + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
@@ -413,13 +432,14 @@ __device__ __forceinline__ void gather8_ext(const real* __restrict__ a, int x, i
 // rho (Eq. 6a, wall rows after the first fill) and aux = psi (P) or rho (FE).
 template <typename real>
 __global__ void rho_walls_kernel(const real* __restrict__ f, real* __restrict__ rho, real* __restrict__ aux,
-                                 const StepParams<real> P, int model, const Ext<real> E) {
+                                 const StepParams<real> P, int model, const Ext<real> E,
+                                 const real* __restrict__ wjy) {
     const long long n = (long long)P.nx * P.ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % P.nx), y = (int)(c / P.nx);
         real v[9];
-        pull_row_ext<true>(f, P, x, x == 0 ? P.nx - 1 : x - 1, x == P.nx - 1 ? 0 : x + 1, y, v);
-        if (E.on && E.g != real(0) && (y == 0 || y == P.ny - 1)) wall_gravity_refill(v, y != 0, P, E);
+        pull_row_ext<true>(f, P, x, x == 0 ? P.nx - 1 : x - 1, x == P.nx - 1 ? 0 : x + 1, y, v, wjy);
+        if (!wjy && E.on && E.g != real(0) && (y == 0 || y == P.ny - 1)) wall_gravity_refill(v, y != 0, P, E);
         const real r = sum9(v);
         rho[c] = r;
         aux[c] = model == 0 ? pseudo_psi(r, P) : r;
@@ -444,7 +464,7 @@ __global__ void mu_walls_kernel(const real* __restrict__ rho, real* __restrict__
 template <typename real>
 __global__ void walls_complete_kernel(real* __restrict__ f, const real* __restrict__ rho,
                                       const real* __restrict__ aux, const StepParams<real> P, int model,
-                                      const Ext<real> E) {
+                                      const Ext<real> E, int onesided) {
     const int nx = P.nx, ny = P.ny;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * nx; k += gridDim.x * blockDim.x) {
         const bool top = k >= nx;
@@ -455,7 +475,8 @@ __global__ void walls_complete_kernel(real* __restrict__ f, const real* __restri
         gather8_ext(aux, x, y, nx, ny, true, an);
         const long long c = (long long)y * nx + x;
         const real Fx = (model == 0 ? an[0] : -rho[c]) * grad_x(an) + P.fx;
-        const real Fy = P.fy - (E.on ? (rho[c] - E.rho_g) * E.g : real(0));
+        const real Fy = P.fy - (E.on ? (rho[c] - E.rho_g) * E.g : real(0)) -
+                        (onesided ? rho[c] * wall_grad_y_onesided(an, top) : real(0));
         wall_fill(v, top, real(-0.5) * Fx, real(-0.5) * Fy);
         // f_i(x, y) = S_i(x - c_i): bottom unknowns 2 (0,1), 5 (1,1), 6 (-1,1) sit in row ny-1;
         // top unknowns 4 (0,-1), 7 (-1,-1), 8 (1,-1) in row 0
@@ -479,7 +500,7 @@ template <typename real>
 __global__ void velocity_ext_kernel(const real* __restrict__ f, const real* __restrict__ rho,
                                     const real* __restrict__ aux, real* __restrict__ ux, real* __restrict__ uy,
                                     const StepParams<real> P, int model, int walls, const Drive<real> D,
-                                    const Ext<real> E) {
+                                    const Ext<real> E, int onesided) {
     const long long n = (long long)P.nx * P.ny;
     const real rave = D.rho_ave ? real(*D.rho_ave) : real(0);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -493,7 +514,9 @@ __global__ void velocity_ext_kernel(const real* __restrict__ f, const real* __re
         const real r = rho[c];
         const real s = model == 0 ? an[0] : -r;
         const real Fx = s * gx + (D.rho_ave ? with_drive(P, D, x, r, rave).fx : P.fx);
-        const real Fy = s * gy + P.fy - (E.on ? (r - E.rho_g) * E.g : real(0));
+        const bool wrow = walls && (y == 0 || y == P.ny - 1);
+        const real Fy = (onesided && wrow ? -r * wall_grad_y_onesided(an, y != 0) : s * gy) + P.fy -
+                        (E.on ? (r - E.rho_g) * E.g : real(0));
         const real jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
         const real jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
         ux[c] = (jx + real(0.5) * Fx) / r;
@@ -566,7 +589,7 @@ __device__ __forceinline__ void fe_collide_iwb(real v[9], real rho, const real m
 template <typename real, int TX, bool WALLS>
 __global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ fin, real* __restrict__ fout,
                                                        const StepParams<real> P, const Drive<real> D,
-                                                       const Ext<real> E) {
+                                                       const Ext<real> E, const real* __restrict__ wjy) {
     __shared__ real s_rho[8][TX + 6];
     __shared__ real s_mu[4][TX + 4];
     __shared__ real s_ux[4][TX + 2];
@@ -600,8 +623,8 @@ __global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ 
     // pulled populations of one row (mapped), with the wall fills of the first kind
     auto pull = [&](int r, real v[9]) {
         const int y = stencil_row<WALLS>(r, ny);
-        pull_row_ext<WALLS>(fin, P, x, xm, xp, y, v);
-        if (WALLS && E.on && E.g != real(0) && (y == 0 || y == ny - 1)) wall_gravity_refill(v, y != 0, P, E);
+        pull_row_ext<WALLS>(fin, P, x, xm, xp, y, v, wjy);
+        if (WALLS && !wjy && E.on && E.g != real(0) && (y == 0 || y == ny - 1)) wall_gravity_refill(v, y != 0, P, E);
     };
     // external force of a cell of row r (mapped row y) with density rho
     auto ext_fx = [&](real rho) { return D.rho_ave ? with_drive(P, D, x, rho, s_rave).fx : P.fx; };
@@ -636,10 +659,12 @@ __global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ 
             mn[0] = m0[mc];
             const real rho = s_rho[cu & 7][rc];
             const bool wall = WALLS && (cu == 0 || cu == ny - 1);
+            // one-sided reading: the wall node's normal -rho d_y mu (zero when mirrored)
+            const real fy_w = (wall && wjy) ? -rho * wall_grad_y_onesided(mn, cu != 0) : real(0);
             if (wall) mirror_neighbours(mn, cu != 0);
             const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
             const real Fx = -rho * grad_x(mn) + ext_fx(rho);
-            const real Fy = -rho * ((mn[2] - mn[4]) * w1 + ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2) + ext_fy(rho);
+            const real Fy = -rho * ((mn[2] - mn[4]) * w1 + ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2) + ext_fy(rho) + fy_w;
             if (wall) wall_fill(p1, cu != 0, real(-0.5) * Fx, real(-0.5) * Fy);
             const real jx = (p1[1] - p1[3]) + (p1[5] - p1[6]) + (p1[8] - p1[7]);
             const real jy = (p1[2] - p1[4]) + (p1[5] + p1[6]) - (p1[7] + p1[8]);
@@ -675,8 +700,10 @@ __global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ 
             rn[0] = rho_c;
             un[0] = x0_[uc];
             vn[0] = y0_[uc];
+            real fy_w = real(0);
             if (WALLS && (c == 0 || c == ny - 1)) {
                 const bool top = c != 0;
+                if (wjy) fy_w = -rho_c * wall_grad_y_onesided(mn, top);
                 mirror_neighbours(mn, top);
                 mirror_neighbours(rn, top);
                 // velocity beyond a no-slip wall: odd extension through u = 0 at the wall node
@@ -689,7 +716,7 @@ __global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ 
                 }
             }
             const real pg = E.on ? E.rho_g * E.g * (real(c) - E.y_ref) : real(0);
-            fe_collide_iwb(p0, rho_c, mn, rn, un, vn, ext_fx(rho_c), ext_fy(rho_c), pg, P, E);
+            fe_collide_iwb(p0, rho_c, mn, rn, un, vn, ext_fx(rho_c), ext_fy(rho_c) + fy_w, pg, P, E);
             const long long o = (long long)c * nx + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
@@ -725,6 +752,70 @@ __global__ void init_iwb_kernel(const src_t* __restrict__ rho0, real* __restrict
             const double r = (double)rho0[shifted_cell(x, y, cxs[i], cys[i], nx, ny)];
             S[i * pitch + c] = (real)(i == 0 ? r - (1.0 - w[0]) * 3.0 * pg : w[i] * 3.0 * pg);
         }
+    }
+}
+
+// One-sided reading of the free-energy walls, the wall rows' densities: a wall node's density
+// is K +- J_y (bottom +, top -) with J_y = -F_y/2 and F_y = -rho d_y mu + fy - (rho - rho_g) g,
+// where d_y mu (wall_grad_y_onesided) depends on mu of the wall row and the next row, which
+// depend on the wall row's densities through the chemical potential and its Laplacian.  One
+// CTA per wall (blockIdx.x: 0 bottom, 1 top) iterates the fixed point `iters` times over the
+// whole row (Jacobi sweeps between CTA barriers; each sweep contracts by about rho c_T^2 / 2)
+// and leaves the converged J_y in wall[0, 2 nx) (bottom then top) for the step and field
+// kernels.  wall[2 nx, 14 nx) is scratch: per wall the first-fill density, the current wall
+// densities, the densities of the next two rows, and mu of the wall row and the next row.
+template <typename real>
+__global__ void __launch_bounds__(256) fe_wall_solve_kernel(const real* __restrict__ fin, const StepParams<real> P,
+                                                            const Ext<real> E, real* __restrict__ wall, int iters) {
+    const int nx = P.nx, ny = P.ny;
+    const bool top = blockIdx.x == 1;
+    const int yw = top ? ny - 1 : 0, y1 = top ? ny - 2 : 1, y2 = top ? ny - 3 : 2;
+    const real sg = top ? real(-1) : real(1);
+    real* Jy = wall + (top ? nx : 0);
+    real* w = wall + 2 * nx + (top ? 6 * nx : 0);
+    real* Kp = w;
+    real* r0 = w + nx;
+    real* r1 = w + 2 * nx;
+    real* r2 = w + 3 * nx;
+    real* m0 = w + 4 * nx;
+    real* m1 = w + 5 * nx;
+    const real jy0 = real(-0.5) * P.fy;  // the first fill's J_y
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        real v[9];
+        pull_row_ext<true>(fin, P, x, xm, xp, yw, v);
+        Kp[x] = r0[x] = sum9(v);
+        pull_row_ext<true>(fin, P, x, xm, xp, y1, v);
+        r1[x] = sum9(v);
+        pull_row_ext<true>(fin, P, x, xm, xp, y2, v);
+        r2[x] = sum9(v);
+    }
+    __syncthreads();
+    for (int it = 0; it < iters; ++it) {
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+            real rn[9];
+            // wall row: the row beyond the wall is the next row, mirrored (Laplacian symmetric)
+            rn[0] = r0[x]; rn[1] = r0[xp]; rn[3] = r0[xm];
+            rn[2] = r1[x]; rn[4] = r1[x]; rn[5] = r1[xp]; rn[8] = r1[xp]; rn[6] = r1[xm]; rn[7] = r1[xm];
+            m0[x] = fe_mu<real>(r0[x], rn, P);
+            // next row: the wall row on one side, the row after on the other
+            rn[0] = r1[x]; rn[1] = r1[xp]; rn[3] = r1[xm];
+            rn[2] = r2[x]; rn[5] = r2[xp]; rn[6] = r2[xm];
+            rn[4] = r0[x]; rn[8] = r0[xp]; rn[7] = r0[xm];
+            m1[x] = fe_mu<real>(r1[x], rn, P);
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+            const real g = real(3) * (real(2.0 / 9.0) * (m1[x] - m0[x]) +
+                                      real(1.0 / 18.0) * ((m1[xp] - m0[xp]) + (m1[xm] - m0[xm])));
+            const real Fy = -r0[x] * (top ? -g : g) + P.fy - (E.on ? (r0[x] - E.rho_g) * E.g : real(0));
+            const real jy = real(-0.5) * Fy;
+            Jy[x] = jy;
+            r0[x] = Kp[x] + sg * (jy - jy0);
+        }
+        __syncthreads();
     }
 }
 

@@ -35,6 +35,7 @@ LBM_F32 = 0
 LBM_F64 = 1
 LBM_BC_PERIODIC = 0
 LBM_BC_WALL_ZOUHE = 1
+LBM_BC_WALL_ZOUHE_ONESIDED = 2
 FLAT = 0
 DROPLET = 1
 
@@ -222,8 +223,10 @@ class Context:
     """Owner of one ``lbm_ctx``.  The workspace is a torch uint8 CUDA tensor and the
     stream a torch stream (its handle is passed to the library)."""
 
-    def __init__(self, params: lbm_params, nx: int, ny: int, stream=None, device="cuda", walls: bool = False):
-        """walls: no-slip walls on rows 0 and ny-1 (Zou-He), else periodic in y."""
+    def __init__(self, params: lbm_params, nx: int, ny: int, stream=None, device="cuda", walls=False):
+        """walls: False (periodic in y), True or LBM_BC_WALL_ZOUHE (no-slip Zou-He walls on rows 0
+        and ny-1), or LBM_BC_WALL_ZOUHE_ONESIDED (the same walls with the free-energy model's
+        one-sided wall-normal chemical-potential gradient)."""
         import torch
 
         self.nx, self.ny = nx, ny
@@ -235,7 +238,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         handle = ctypes.c_void_p()
         rc = _lib().lbm_create(ctypes.byref(params), nx, ny, LBM_BC_PERIODIC,
-                               LBM_BC_WALL_ZOUHE if walls else LBM_BC_PERIODIC,
+                               (LBM_BC_WALL_ZOUHE if walls is True else int(walls)) if walls else LBM_BC_PERIODIC,
                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.c_void_p(aligned),
                                ctypes.c_size_t(nbytes), ctypes.byref(handle))
         _check(rc, "lbm_create")

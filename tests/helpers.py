@@ -6,11 +6,12 @@ import oracle as O
 
 def oracle_params(rp, th, walls=False):
     """Oracle parameters equal to a resolved ``lbm_params`` (rp) and its thermodynamics (th);
-    walls: no-slip walls on rows 0 and ny-1."""
+    walls: no-slip walls on rows 0 and ny-1 (1 or True: mirrored reading, 2: the free-energy
+    one-sided wall-normal chemical-potential gradient)."""
     return O.make_params(a=rp.a, b=rp.b, R=rp.R, T=th.T, tau_rho=1.0, tau_e=rp.tau_e, tau_zeta=rp.tau_zeta,
                          tau_q=rp.tau_q, tau_j=rp.tau_j, tau_nu=rp.tau_nu, kappa_P=rp.kappa_P,
                          kappa_Li=rp.kappa_Li, sigma_Li=rp.sigma_Li, kappa=rp.kappa, fx=rp.body_fx,
-                         fy=rp.body_fy, walls=1.0 if walls else 0.0, A=rp.A)
+                         fy=rp.body_fy, walls=float(walls) if walls else 0.0, A=rp.A)
 
 
 def gpu_context(model, precision, nx, ny, walls=False, **kw):

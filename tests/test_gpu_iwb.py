@@ -67,6 +67,19 @@ def test_fp64_A_gravity_walls(shape):
     _compare(ctx, rp, th, rho0, 40, walls=True, g=1e-5, rho_g=th.rho_l, y_ref=ny / 2)
 
 
+def test_fp64_A_gravity_onesided_walls():
+    """A = 0.1 with gravity (g = 1e-5, rho_0 = rho_l) between one-sided free-energy walls, body
+    force along x, sine-perturbed channel: every population after 40 steps."""
+    nx, ny = 70, 42
+    ctx, rp, th = gpu_context(FE, F64, nx, ny, walls=2, a=0.25, Tr=0.8, tau_nu=1.0, tau_e=1.0, A=0.1,
+                              body_fx=1e-5)
+    ctx.set_gravity(1e-5, th.rho_l, ny / 2)
+    rho0 = inputs.plate_channel(nx, ny, th.rho_v, th.rho_l, amp=3.0)
+    ctx.set_density(rho0)
+    ctx.step(40)
+    _compare(ctx, rp, th, rho0, 40, walls=2, g=1e-5, rho_g=th.rho_l, y_ref=ny / 2)
+
+
 def test_fp64_weight_periodic_with_drive():
     """Plain weight (rho_0 = 0) on a periodic droplet pair with the Sec. 5.4 drive switched on
     at t = 5 (A = 0): 70 steps across the switch-on."""
