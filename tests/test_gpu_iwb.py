@@ -130,3 +130,27 @@ def test_shear_wave_viscosity_gpu(A, tau):
         amps.append(2.0 / L * np.sum(ux[:, 0] * np.sin(2 * np.pi * y / L)))
     nu = -np.log(amps[1] / amps[0]) / ((2 * np.pi / L) ** 2 * 1000)
     assert abs(nu / ((tau - 0.5 - A) / 3.0) - 1) < 5e-3, nu
+
+
+def test_gravity_and_drive_argument_errors():
+    """lbm_set_gravity: pseudopotential contexts and p_g on a periodic lattice (rho_ref != 0
+    without walls) are refused, non-finite values are argument errors; lbm_set_drive on a
+    walled lattice is refused (its reduction sums a periodic lattice's populations)."""
+    from paper_2403_11167_gb300 import lbm
+
+    ctx, _, _ = gpu_context(0, F64, 16, 8, a=0.25, Tr=0.8)
+    with pytest.raises(lbm.LBMError) as e:
+        ctx.set_gravity(1e-5, 0.0)
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+    ctx, _, th = gpu_context(FE, F64, 16, 8, a=0.25, Tr=0.8)
+    with pytest.raises(lbm.LBMError) as e:
+        ctx.set_gravity(1e-5, th.rho_l)
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+    with pytest.raises(lbm.LBMError) as e:
+        ctx.set_gravity(float("nan"), 0.0)
+    assert e.value.code == lbm.LBM_ERR_ARG
+    ctx.set_gravity(1e-5, 0.0)  # plain weight on a periodic lattice is fine
+    ctx, _, _ = gpu_context(FE, F64, 16, 8, walls=True, a=0.25, Tr=0.8)
+    with pytest.raises(lbm.LBMError) as e:
+        ctx.set_drive(1e-6, -1e-6, 8, 0)
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
