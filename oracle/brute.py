@@ -168,10 +168,12 @@ def fe_step(f, pr):
     grad p_g, the buoyancy -(rho - rho_0) g, the Sec. 5.4 drive and, with walls, the Zou-He
     rows (u = 0 with the half force: J = -F/2), mirrored stencils and odd velocities beyond
     the walls.  Optional keys: A, g, rho_g, y_ref, walls, drive, drive_ax_lo, drive_ax_hi,
-    drive_x_split."""
+    drive_x_split.  walls = 2: the wall rows' normal grad mu one-sided (ghost 2 mu(0) - mu(1))
+    with the wall densities iterated to the fixed point of fill and normal force."""
     f = f.copy()
     ny, nx = f.shape[1:]
     walls = bool(pr.get("walls", 0.0))
+    one_sided = pr.get("walls", 0.0) == 2.0
     A, g, rg, yref = pr.get("A", 0.0), pr.get("g", 0.0), pr.get("rho_g", 0.0), pr.get("y_ref", 0.0)
     yv = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
     wall_row = np.zeros((ny, nx), bool)
@@ -179,7 +181,7 @@ def fe_step(f, pr):
         wall_row[[0, -1]] = True
         zou_he(f, np.zeros((ny, nx)), np.full((ny, nx), -pr["fy"] / 2))
     rho = f.sum(0)
-    if walls and g != 0.0:
+    if walls and not one_sided and g != 0.0:
         # wall rows: the node's own buoyancy enters its normal force; rho = K + Jy (bottom),
         # K - Jy (top), Jy = -(fy - (rho - rho_0) g)/2
         K0 = rho[0] + pr["fy"] / 2
@@ -191,6 +193,24 @@ def fe_step(f, pr):
         Fyw[-1] = pr["fy"] - (r1 - rg) * g
         zou_he(f, np.zeros((ny, nx)), -Fyw / 2)
         rho = f.sum(0)
+    def wall_dmu(mu):
+        # one-sided wall-normal gradient at rows 0 and ny-1 (Eq. 24 weights, extrapolated ghost)
+        g = np.zeros((ny, nx))
+        for y, yi, sgn in ((0, 1, 1.0), (ny - 1, ny - 2, -1.0)):
+            d = mu[yi] - mu[y]
+            g[y] = sgn * 2 * (W[2] * d + W[5] * (np.roll(d, -1) + np.roll(d, 1))) / CS2
+        return g
+
+    if one_sided:
+        for _ in range(200):
+            mu = mu_bulk(rho, pr["a"], pr["b"], pr["R"], pr["T"]) - pr["kappa"] * lap(rho, True)
+            Fyw = -rho * wall_dmu(mu) + pr["fy"] - (rho - rg) * g
+            zou_he(f, np.zeros((ny, nx)), -Fyw / 2)
+            new = f.sum(0)
+            done = np.abs(new - rho).max() <= 1e-16 * rho[0, 0]
+            rho = new
+            if done:
+                break
     mu = mu_bulk(rho, pr["a"], pr["b"], pr["R"], pr["T"]) - pr["kappa"] * lap(rho, walls)
     Fx_ext = pr["fx"] * np.ones((ny, nx))
     if pr.get("drive", 0.0):
@@ -198,7 +218,7 @@ def fe_step(f, pr):
         Fx_ext = Fx_ext + ax * np.abs(rho - rho.mean())
     F = -rho * grad(mu, walls) + np.stack([Fx_ext, pr["fy"] - (rho - rg) * g])
     grho = grad(rho, walls)
-    F[1][wall_row] = (pr["fy"] - (rho - rg) * g)[wall_row]
+    F[1][wall_row] = (pr["fy"] - (rho - rg) * g - (rho * wall_dmu(mu) if one_sided else 0.0))[wall_row]
     grho[1][wall_row] = 0.0
     if walls:
         zou_he(f, -F[0] / 2, -F[1] / 2)

@@ -222,6 +222,8 @@ def _wall_unknown_mask(ny, nx):
     (O.FE, dict(A=-0.1, walls=1.0)),
     (O.FE, dict(g=3e-4, rho_g=0.0)),
     (O.FE, dict(A=0.1, walls=1.0, g=2e-5, rho_g=0.1, y_ref=3.0)),
+    (O.FE, dict(walls=2.0)),
+    (O.FE, dict(A=0.1, walls=2.0, g=2e-5, rho_g=0.1, y_ref=3.0)),
 ])
 def test_brute_force_agreement_extensions(model, extra):
     """The walls (Zou-He fill, mirrored stencils, odd velocities), the Sec. 5.4 drive, the
