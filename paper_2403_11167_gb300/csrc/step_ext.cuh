@@ -759,13 +759,13 @@ __global__ void init_iwb_kernel(const src_t* __restrict__ rho0, real* __restrict
 // is K +- J_y (bottom +, top -) with J_y = -F_y/2 and F_y = -rho d_y mu + fy - (rho - rho_g) g,
 // where d_y mu (wall_grad_y_onesided) depends on mu of the wall row and the next row, which
 // depend on the wall row's densities through the chemical potential and its Laplacian.  One
-// CTA per wall (blockIdx.x: 0 bottom, 1 top) iterates the fixed point `iters` times over the
+// CTA per wall (blockIdx.x: 0 bottom, 1 top; 1024 threads) iterates the fixed point `iters` times over the
 // whole row (Jacobi sweeps between CTA barriers; each sweep contracts by about rho c_T^2 / 2)
 // and leaves the converged J_y in wall[0, 2 nx) (bottom then top) for the step and field
 // kernels.  wall[2 nx, 14 nx) is scratch: per wall the first-fill density, the current wall
 // densities, the densities of the next two rows, and mu of the wall row and the next row.
 template <typename real>
-__global__ void __launch_bounds__(256) fe_wall_solve_kernel(const real* __restrict__ fin, const StepParams<real> P,
+__global__ void __launch_bounds__(1024) fe_wall_solve_kernel(const real* __restrict__ fin, const StepParams<real> P,
                                                             const Ext<real> E, real* __restrict__ wall, int iters) {
     const int nx = P.nx, ny = P.ny;
     const bool top = blockIdx.x == 1;
