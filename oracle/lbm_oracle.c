@@ -523,11 +523,11 @@ static void fe_wall_density(const orc_params* p, int nx, int ny, double* f, doub
                 size_t c = (size_t)y * nx + x;
                 double s = 0.0;
                 for (int i = 0; i < Q9; ++i) s += f[(size_t)i * N + c];
-                dmax = fmax(dmax, fabs(s - rho[c]));
+                dmax = fmax(dmax, fabs(s - rho[c]) / s);
                 rho[c] = s;
             }
         }
-        if (dmax <= 1e-16 * rho[0]) break;
+        if (dmax <= 4e-16) break;  /* rounding level (reached in 16-29 sweeps) */
     }
 }
 
