@@ -350,7 +350,7 @@ def run_walls(args, peak):
 def run_surrogate(args):
     """Learned calibration surrogate: label seeded parameter sets (Tr, a, b, kappa_P) with the
     batched solver (flat slab + three width-scaled droplets each), train the MLP on the GPU,
-    and judge it against the calibration runs of 256 held-out sets (batched; a sample of them
+    and measure it against the calibration runs of 256 held-out sets (batched; a sample of them
     also through the plain one-lattice-at-a-time API, which must agree bitwise).  Reports the
     per-set cost of a plain calibration, of a batched one, and of a surrogate query (4096
     queries per fused BF16 launch, CUDA events), held-out errors, and the gain over the

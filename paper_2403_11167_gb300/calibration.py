@@ -22,7 +22,7 @@ and some of their slabs never settle.  Wide interfaces, Tr > 0.9, need the large
 the width scaling gives them.)
 
 ``calibrate_batched`` runs many sets as ``lbm_batch`` sweeps; ``calibrate_plain`` runs the
-same lattices one ``lbm_ctx`` at a time (the plain calibration that judges the surrogate).
+same lattices one ``lbm_ctx`` at a time (the plain calibration, the reference of the surrogate).
 Both are bitwise the same computation.  ``fit_surrogate`` trains the MLP on the GPU.
 """
 from __future__ import annotations

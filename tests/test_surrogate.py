@@ -210,7 +210,7 @@ def test_calibration_data_quality(calibrated):
 
 
 def test_batched_calibration_equals_plain_calibration(calibrated):
-    """The plain calibration (one lbm_ctx per lattice) judges the surrogate; the batched sweep
+    """The plain calibration (one lbm_ctx per lattice) is the surrogate's reference; the batched sweep
     that labels the held-out sets is bitwise the same computation (three sets checked)."""
     C, ho, rh = calibrated["C"], calibrated["ho"], calibrated["rh"]
     rp = C.calibrate_plain(ho[:3])
