@@ -100,3 +100,27 @@ def test_two_phase_plate_flow_against_eq89(model, tol):
     assert np.abs(ux[:, 0] - ua).max() < tol * ua.max()
     assert np.abs(ux - ux[:, :1]).max() < 1e-14 * ua.max()    # uniform in x
     assert np.abs(uy).max() < 1e-6 * ua.max()
+
+
+@pytest.mark.parametrize("model,band", [(O.PP, 2), (O.FE, 3)])
+def test_wall_band_widths(model, band):
+    """The walled step differs from the periodic one only near the walls: after one step of
+    the same random state, the periodic and walled oracles agree bitwise on every row at least
+    band + 1 rows from a wall (band = 2 for P: psi one row away; 3 for FE: mu one row away and
+    rho one more; the + 1 is streaming), and differ on the row band rows from a wall -- the
+    rows a GPU strip step must recompute with the wall kernel."""
+    nx, ny = 8, 20
+    a = 0.5
+    T = thermo.temperature(a, 4.0, 1.0, 0.8)
+    rv, rl, _ = thermo.maxwell(a, 4.0, 1.0, 0.8)
+    rng = np.random.Generator(np.random.PCG64(21))
+    rho0 = rng.uniform(rv * 1.5, rl * 0.8, (ny, nx))
+    kw = dict(a=a, b=4.0, R=1.0, T=T, tau_nu=0.9, tau_e=0.85, kappa=0.5, fx=1e-5, fy=-2e-5)
+    if model == O.PP:
+        kw.update(sigma_Li=0.1, kappa_P=0.7, tau_q=1 / 1.99)
+    f0 = O.init(model, rho0)
+    fp = O.run(model, O.make_params(**kw), f0, 1)
+    fw = O.run(model, O.make_params(walls=1.0, **kw), f0, 1)
+    same = np.all(fp == fw, axis=(0, 2))
+    assert same[band + 1:ny - band - 1].all()
+    assert not same[band] and not same[ny - 1 - band]
