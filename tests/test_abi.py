@@ -89,3 +89,25 @@ def test_argument_errors(lib):
     assert lib.lbm_workspace_bytes(0, 0, 5) == 0
     assert lib.lbm_workspace_bytes(1, 256, 4) > 2 * 9 * 256 * 4 * 8
     assert "sm_103a" in lib.lbm_build_info()
+
+
+def test_create_rejects_bad_sizes_and_boundaries_before_any_device_call(lib):
+    """lbm_create validates sizes and boundaries before touching the device (so this runs
+    without a GPU): empty lattices and more than 2^31 cells are argument errors, walls need
+    ny >= 4, walls in x are not built; *out is left NULL."""
+    L = lib._lib()
+    p = lib.lbm_params_default(lib.LBM_FREE_ENERGY)
+    cases = [((0, 5, lib.LBM_BC_PERIODIC, lib.LBM_BC_PERIODIC), lib.LBM_ERR_ARG),
+             ((5, 0, lib.LBM_BC_PERIODIC, lib.LBM_BC_PERIODIC), lib.LBM_ERR_ARG),
+             ((1 << 16, (1 << 15) + 1, lib.LBM_BC_PERIODIC, lib.LBM_BC_PERIODIC), lib.LBM_ERR_ARG),
+             ((16, 3, lib.LBM_BC_PERIODIC, lib.LBM_BC_WALL_ZOUHE), lib.LBM_ERR_ARG),
+             ((16, 3, lib.LBM_BC_PERIODIC, lib.LBM_BC_WALL_ZOUHE_ONESIDED), lib.LBM_ERR_ARG),
+             ((16, 8, lib.LBM_BC_WALL_ZOUHE, lib.LBM_BC_PERIODIC), lib.LBM_ERR_UNSUPPORTED),
+             ((16, 8, lib.LBM_BC_PERIODIC, 7), lib.LBM_ERR_UNSUPPORTED)]
+    for (nx, ny, bx, by), code in cases:
+        h = ctypes.c_void_p(1)
+        rc = L.lbm_create(ctypes.byref(p), nx, ny, bx, by, None, None, ctypes.c_size_t(0), ctypes.byref(h))
+        assert rc == code, ((nx, ny, bx, by), rc)
+        assert h.value is None
+    # the workspace a context needs grows with the lattice and covers the one-sided walls' scratch
+    assert lib.lbm_workspace_bytes(0, 64, 64) > 2 * 9 * 64 * 64 * 4 + 14 * 64 * 4
