@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--ref-seconds", type=float, default=None,
                     help="reference arm: seconds of oracle work per timed step (default: ~1 min in total)")
     ap.add_argument("--plain-sets", type=int, default=6, help="held-out sets also calibrated one lattice at a time")
+    ap.add_argument("--profile", choices=["pp", "fe"], default=None,
+                    help="profiler workload: --steps single-step launches of one model's FP32 step on the "
+                         "--size^2 spinodal lattice (for ncu -k regex:<model>_step), no JSON line")
+    ap.add_argument("--A", type=float, default=0.0, help="--profile fe with A != 0 runs the full-model kernel")
     return ap.parse_args()
 
 
@@ -91,32 +95,47 @@ def workload_config(args):
     }
 
 
-def make_rho0(size):
-    from paper_2403_11167_gb300 import inputs, lbm
+def make_rho0(size, rho_v, rho_l):
+    """The workload's initial density from the coexistence densities of its parameters."""
+    from paper_2403_11167_gb300 import inputs
 
-    _, th = lbm.lbm_resolve_params(lbm.lbm_params_default(0, a=0.25, Tr=0.85, tau_nu=0.8))
-    return inputs.spinodal_noise(size, size, 0.5 * (th.rho_l + th.rho_v), 0.01, seed=2403)
+    return inputs.spinodal_noise(size, size, 0.5 * (rho_l + rho_v), 0.01, seed=2403)
 
 
 # --------------------------------------------------------------------------------------
-# CPU oracle (reference arm and cpu_baseline)
+# CPU oracle (reference arm and cpu_baseline).  Everything on this leg -- the temperature,
+# the coexistence densities, sigma^Li and the default relaxation times (tau_nu = tau; P:
+# tau_e = tau_zeta = tau, tau_q = 1/1.99; FE: tau_e = 1/4 + tau/2) -- comes from the oracle
+# package; the product library is not loaded.
 
-def oracle_mlups(rho0, seconds, crop=512):
+def oracle_workload():
+    """(rho_v, rho_l, [oracle parameters of the P and FE models]) of the throughput workload
+    (Carnahan-Starling a = 0.25, b = 4, R = 1, Tr = 0.85, tau = 0.8, kappa = 0.5)."""
+    import oracle as O
+    from oracle import thermo
+
+    a, b, R, Tr, tau = 0.25, 4.0, 1.0, 0.85, 0.8
+    T = thermo.temperature(a, b, R, Tr)
+    rho_v, rho_l, _ = thermo.maxwell(a, b, R, Tr)
+    sigma_li = thermo.sigma_li(a, b, R, Tr)[0]
+    pp = O.make_params(a=a, b=b, R=R, T=T, tau_e=tau, tau_zeta=tau, tau_q=1.0 / 1.99, tau_j=1.0, tau_nu=tau,
+                       kappa_P=1.0, kappa_Li=0.0, sigma_Li=sigma_li)
+    fe = O.make_params(a=a, b=b, R=R, T=T, tau_e=0.25 + 0.5 * tau, tau_zeta=1.0, tau_q=1.0, tau_j=1.0,
+                       tau_nu=tau, kappa=0.5)
+    return rho_v, rho_l, [pp, fe]
+
+
+def oracle_mlups(size, seconds, crop=512):
     """Time the FP64 oracle, as it stands, on a crop of the workload: both models, the
-    number of steps grown until about ``seconds`` of CPU work."""
+    number of steps grown until about ``seconds`` of CPU work.  Returns (MLUPS, threads,
+    sample description, seconds of oracle work)."""
     import numpy as np
 
     import oracle as O
-    from paper_2403_11167_gb300 import lbm
 
-    sub = np.ascontiguousarray(rho0[:crop, :crop])
+    rho_v, rho_l, cfgs = oracle_workload()
+    sub = np.ascontiguousarray(make_rho0(size, rho_v, rho_l)[:crop, :crop])
     updates, elapsed, steps = 0, 0.0, 1
-    cfgs = []
-    for model in (0, 1):
-        rp, th = lbm.lbm_resolve_params(lbm.lbm_params_default(model, a=0.25, Tr=0.85, tau_nu=0.8))
-        cfgs.append(O.make_params(a=rp.a, b=rp.b, R=rp.R, T=th.T, tau_e=rp.tau_e, tau_zeta=rp.tau_zeta,
-                                  tau_q=rp.tau_q, tau_j=rp.tau_j, tau_nu=rp.tau_nu, kappa_P=rp.kappa_P,
-                                  kappa_Li=rp.kappa_Li, sigma_Li=rp.sigma_Li, kappa=rp.kappa))
     while elapsed < seconds:
         for model in (0, 1):
             f = O.init(model, sub)
@@ -126,26 +145,29 @@ def oracle_mlups(rho0, seconds, crop=512):
             updates += sub.size * steps
         steps *= 2
     return updates / elapsed / 1e6, O.num_threads(), f"{crop}x{crop} crop of the workload, both models, " \
-        f"{updates // sub.size} lattice steps in total, FP64"
+        f"{updates // sub.size} lattice steps in total, FP64", elapsed
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    rho0 = make_rho0(args.size)
     per_step = args.ref_seconds or max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_mlups(rho0, per_step / 4)
-    vals, cores, sample = [], 1, ""
+        oracle_mlups(args.size, per_step / 4)
+    vals, secs, cores, sample = [], [], 1, ""
     for _ in range(args.steps):
-        v, cores, sample = oracle_mlups(rho0, per_step)
+        v, cores, sample, sec = oracle_mlups(args.size, per_step)
         vals.append(v)
+        secs.append(sec)
     value = sum(vals) / len(vals)
     cell_updates = 2 * args.lbm_steps * args.size * args.size
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cell_updates / (value * 1e6) * 1e3,
+        "steps": args.steps, "warmup": args.warmup,
+        # a timed step is one bounded sample of the workload (see cpu_baseline.sample)
+        "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "ms_per_step_extrapolated_full_workload": cell_updates / (value * 1e6) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
@@ -423,12 +445,12 @@ def run_surrogate(args):
     }
 
 
-KERNEL_SOURCES = ("lbm_kernels.cuh", "step_tma.cuh", "step_warp.cuh", "step_pair.cuh")
+KERNEL_SOURCES = ("lbm_kernels.cuh", "ring.cuh", "step_pair.cuh")
 
 
 def kernel_source_hash():
-    """First 12 hex digits of the SHA-256 of the step kernels' sources (per-cell arithmetic and
-    the TMA strip pipeline), concatenated in KERNEL_SOURCES order."""
+    """First 12 hex digits of the SHA-256 of the step kernels' sources (per-cell arithmetic, the
+    row ring and the strip kernels), concatenated in KERNEL_SOURCES order."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2403_11167_gb300", "csrc", name), "rb") as fh:
@@ -483,7 +505,8 @@ def run_ours(args):
 
     size, nsteps = args.size, args.lbm_steps
     ncell = size * size
-    rho0 = make_rho0(size)
+    _, th = lbm.lbm_resolve_params(lbm.lbm_params_default(0, a=0.25, Tr=0.85, tau_nu=0.8))
+    rho0 = make_rho0(size, th.rho_v, th.rho_l)
     stream = torch.cuda.Stream()
     ctxs = []
     for model in (0, 1):
@@ -571,7 +594,7 @@ def run_ours(args):
         walls = run_walls(args, peak)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        v, cores, sample = oracle_mlups(rho0, args.cpu_seconds)
+        v, cores, sample, _ = oracle_mlups(size, args.cpu_seconds)
         cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample}
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
@@ -589,9 +612,33 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile(args):
+    """Small fixed workload for ncu captures of one step kernel (see --profile)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2403_11167_gb300 import inputs, lbm
+
+    model = lbm.LBM_PSEUDOPOTENTIAL if args.profile == "pp" else lbm.LBM_FREE_ENERGY
+    p = lbm.lbm_params_default(model, precision=lbm.LBM_F32, a=0.25, Tr=0.85, tau_nu=0.8, A=args.A)
+    ctx = lbm.Context(p, args.size, args.size)
+    _, th = ctx.derived()
+    ctx.set_density(inputs.spinodal_noise(args.size, args.size, 0.5 * (th.rho_l + th.rho_v), 0.01, seed=2403))
+    for _ in range(args.steps):
+        ctx.step(1)
+    ctx.synchronize()
+    torch.cuda.synchronize()
+    print("profile workload done:", args.profile, args.size, args.steps)
+    ctx.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -12,7 +12,9 @@
  *   LBM_FREE_ENERGY      the improved well-balanced free-energy model (Sec. 2.2):
  *                        Eq. (1) MRT step with chemical potential mu = mu_b - kappa
  *                        lap rho (Eq. 29, stencils of Eq. 24), equilibrium Eq. (20)
- *                        and forcing Eq. (21), with A = 0 and no gravity.
+ *                        and forcing Eq. (21), including the viscosity-tuning term A
+ *                        (lbm_params.A, Eqs. 20 and 23) and gravity (lbm_set_gravity:
+ *                        p_g in Eq. 20, -grad p_g in Eq. 21, buoyancy).
  *
  * Units are lattice units: dx = dt = c = 1, c_s^2 = 1/3, G = -1 (Sec. 2.1).
  *
@@ -27,7 +29,10 @@
  *   - all GPU work of a context runs on the context's stream, in call order.
  *     Functions that return host data synchronise that stream first.
  *   - populations are stored as 9 planes f_i[y][x] (structure of arrays) of the
- *     context precision; host-side population arrays use the velocity order of
+ *     context precision; FP32 buffers have a tenth plane of int16 values that extends the
+ *     free-energy model's rest population by 16 bits (f_0 = plane 0 + q 2^-16 ulp(plane
+ *     0): in that model f_0 carries almost all of the mass, and FP32 rounding of it
+ *     would random-walk the mass); host-side population arrays use the velocity order of
  *     Eq. (2) (0 rest, 1..4 = (1,0),(0,1),(-1,0),(0,-1), 5..8 = (1,1),(-1,1),
  *     (-1,-1),(1,-1)), shape [9][ny][nx], row-major, FP64.
  */
@@ -43,7 +48,8 @@ extern "C" {
 /* status codes */
 #define LBM_OK 0
 #define LBM_ERR_ARG (-1)          /* invalid argument (size, tau <= 1/2, Tr outside (0,1), ...) */
-#define LBM_ERR_UNSUPPORTED (-2)  /* feature not built (walls in x, A != 0, ...) */
+#define LBM_ERR_UNSUPPORTED (-2)  /* feature not built (walls in x, A != 0 or gravity with the
+                                     pseudopotential model, ...) */
 #define LBM_ERR_CUDA (-3)         /* a CUDA runtime call failed */
 #define LBM_ERR_DIVERGED (-4)     /* NaN/Inf or rho <= 0 seen; sticky for the context */
 #define LBM_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
@@ -120,8 +126,10 @@ int lbm_params_default(int model, lbm_params* p);
  * fill *th (either may alias nothing; out and th must be non-NULL).  Follows
  * Sec. 3 and Appendix B: critical point, Maxwell densities, sigma_Li by Newton's
  * method with Simpson quadrature of Eqs. (S13)-(S14) from eps = 2, and the
- * optional width/surface-tension match.  Errors: LBM_ERR_ARG for invalid inputs,
- * LBM_ERR_NOCONVERGE if a solve fails, LBM_ERR_UNSUPPORTED for A != 0. */
+ * optional width/surface-tension match.  Errors: LBM_ERR_ARG for invalid inputs
+ * (including A with nu = c_s^2 (tau_nu - 1/2 - A) <= 0, Eq. 23), LBM_ERR_NOCONVERGE if a
+ * solve fails, LBM_ERR_UNSUPPORTED for A != 0 with the pseudopotential model (A is a term
+ * of the free-energy equilibrium, Eq. 20; the free-energy model accepts it). */
 int lbm_resolve_params(const lbm_params* in, lbm_params* out, lbm_thermo* th);
 
 /* Host-only: lbm_resolve_params on each of in[0..n-1], spread over the host's cores
@@ -213,8 +221,9 @@ int lbm_get_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy);
  * a few hundred values, for probing very large lattices without a full download. */
 int lbm_get_populations_at(lbm_ctx* ctx, int n, const int* xs, const int* ys, double* out);
 
-/* Device pointer of the current population buffer (9 planes, context precision) and
- * its plane pitch in elements (plane p starts at p * pitch). */
+/* Device pointer of the current population buffer (9 planes, context precision; FP32
+ * buffers also hold the int16 rest-population plane at 9 * pitch elements) and its plane
+ * pitch in elements (plane p starts at p * pitch). */
 int lbm_device_populations(lbm_ctx* ctx, void** f, long long* plane_pitch);
 
 /* Maximum number of reduction blocks lbm_observables_fields_static accepts. */
@@ -254,9 +263,9 @@ int lbm_observables_fields_static(int precision, const void* rho, const void* ux
 /* ---------------------------------------------------------------------------------- */
 /* Batched calibration sweep (pseudopotential model, FP32).                             */
 /* The paper tunes sigma_Li, kappa_P and kappa_Li against coexistence densities, width  */
-/* and surface tension (Sec. 3, App. B) and notes that the pseudopotential model needs  */
-/* previous simulations to fix its parameters (Sec. 5.1-5.2).  A batch runs many such   */
-/* independent lattices at once on one GPU.                                             */
+/* and surface tension (Sec. 3, App. B); the pseudopotential model's parameters are set */
+/* from preliminary runs (Secs. 5.1-5.2).  A batch runs many such independent lattices  */
+/* at once on one GPU.                                                                  */
 
 typedef struct {
     int nx, ny;          /* lattice size (periodic); nx % 4 == 0 unless the lattice is resident */
@@ -368,7 +377,11 @@ void lbm_surrogate_destroy(lbm_surrogate* m);
 /* Text of the last CUDA failure of a surrogate call on this host thread. */
 const char* lbm_surrogate_last_error(void);
 
-/* Checkpoint: write/read the populations, step counter and parameters (binary). */
+/* Checkpoint: write/read the populations (FP64, the FP32 free-energy rest population with its
+ * extension), step counter and resolved parameters (binary).  lbm_load returns LBM_ERR_ARG when
+ * the file's lattice size, model, precision or any resolved parameter differs from the
+ * context's (a state of one temperature or EOS is not a state of another), LBM_ERR_IO when the
+ * file cannot be read. */
 int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);
 

@@ -1,8 +1,8 @@
 // batch.cu -- batched calibration sweep: many independent pseudopotential lattices at once.
 //
 // The calibration runs the pseudopotential model needs (Sec. 3: sigma^Li, kappa^P and
-// kappa^Li tuned against coexistence densities, interface width and surface tension, and
-// Sec. 5.2: "previous simulations to determine parameters") are many small, independent
+// kappa^Li tuned against coexistence densities, interface width and surface tension; Secs.
+// 5.1-5.2: its parameters are set from preliminary runs) are many small, independent
 // lattices of uneven sizes and step counts.  Run one at a time, the small ones are
 // launch-latency bound and the large ones leave most SMs idle.  Here they run together:
 //
@@ -33,7 +33,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
-#include "step_tma.cuh"
+#include "ring.cuh"
 #include "step_pair.cuh"
 
 namespace {
@@ -49,16 +49,9 @@ int bfail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return bfail(e_, #call);       \
     } while (0)
 
-constexpr int kBTX = 256;        // strip width of the one-cell tiled batch kernel
-constexpr int kBS = 6;           // its stage count
-// Tiled lattices run the two-cells-per-lane strip of the context path (1) or the one-cell
-// CTA-synchronised strip (0).
-#ifndef LBM_BATCH_PAIR
-#define LBM_BATCH_PAIR 1
-#endif
-constexpr bool kBPair = LBM_BATCH_PAIR != 0;
 constexpr int kBPWarps = 4;
 constexpr int kBPStages = 6;
+static_assert(kBPStages >= 4, "the pseudopotential strip ring needs at least 4 stages");
 using BPSmem = lbmk::WarpStripSmem<kBPWarps, kBPStages, 60>;
 constexpr int kBPTX = BPSmem::TX;  // widest pair strip (240 columns)
 constexpr int kChunk = 64;       // steps per captured graph
@@ -141,21 +134,6 @@ __global__ void __launch_bounds__(1024, 1)
         const int i = idx / N, c = idx - i * N;
         g[i * pitch + c] = S[idx];
     }
-}
-
-// Tiled lattices: one strip of one lattice per CTA, one time step per launch.
-template <int TX, int S>
-__global__ void __launch_bounds__(TX + 32, LBM_PP_MINB)
-    pp_batch_tma(const BatchLattice* __restrict__ lats, const BatchItem* __restrict__ items,
-                 const int* __restrict__ step_base, int k, int* __restrict__ err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    PPTmaSmem<TX, S>& sm = *reinterpret_cast<PPTmaSmem<TX, S>*>(smem_raw);
-    const BatchItem it = items[blockIdx.x];
-    const BatchLattice& L = lats[it.lat];
-    const int step = *step_base + k;
-    if (step >= L.nsteps) return;
-    const StepParams<float> P = L.P;
-    pp_strip_tma<TX, S>(L.buf[step & 1], L.buf[(step + 1) & 1], P, it.x0, it.w, it.y0, it.y1, sm, err);
 }
 
 // Tiled lattices, two cells per lane: one strip of one lattice per CTA, one step per launch.
@@ -340,12 +318,8 @@ int launch_resident(lbm_batch* b, int step_limit, cudaStream_t s) {
 
 int launch_tiled_step(lbm_batch* b, int k, cudaStream_t s) {
     if (b->items.empty()) return LBM_OK;
-    if (kBPair)
-        lbmk::pp_batch_pair<kBPWarps, kBPStages><<<(unsigned)b->items.size(), (kBPWarps + 1) * 32, sizeof(BPSmem), s>>>(
-            b->d_lat, b->d_items, b->d_step, k, b->d_err);
-    else
-        lbmk::pp_batch_tma<kBTX, kBS><<<(unsigned)b->items.size(), kBTX + 32, sizeof(lbmk::PPTmaSmem<kBTX, kBS>), s>>>(
-            b->d_lat, b->d_items, b->d_step, k, b->d_err);
+    lbmk::pp_batch_pair<kBPWarps, kBPStages><<<(unsigned)b->items.size(), (kBPWarps + 1) * 32, sizeof(BPSmem), s>>>(
+        b->d_lat, b->d_items, b->d_step, k, b->d_err);
     BCK(cudaGetLastError());
     return LBM_OK;
 }
@@ -363,7 +337,7 @@ void build_items(lbm_batch* b, int rows) {
         b->lat[i].P.rows = r;
         // pair strips: nx split into equal widths (multiples of 4, at most kBPTX columns)
         const int gx = (nx + kBPTX - 1) / kBPTX;
-        const int wb = kBPair ? lbmk::warp_strip_width(nx, gx) : kBTX;
+        const int wb = lbmk::warp_strip_width(nx, gx);
         for (int y0 = 0; y0 < ny; y0 += r)
             for (int x0 = 0; x0 < nx; x0 += wb)
                 b->items.push_back(BatchItem{i, x0, std::min(wb, nx - x0), y0, std::min(y0 + r, ny)});
@@ -627,9 +601,7 @@ extern "C" int lbm_batch_create(int n, const lbm_batch_lattice* specs, const dou
                                       (int)smax)) != cudaSuccess)
             return fail(bfail(e, "cudaFuncSetAttribute(resident smem)"));
     }
-    if ((e = cudaFuncSetAttribute(lbmk::pp_batch_tma<kBTX, kBS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sizeof(lbmk::PPTmaSmem<kBTX, kBS>))) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(lbmk::pp_batch_pair<kBPWarps, kBPStages>,
+    if ((e = cudaFuncSetAttribute(lbmk::pp_batch_pair<kBPWarps, kBPStages>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BPSmem))) != cudaSuccess)
         return fail(bfail(e, "cudaFuncSetAttribute(batch strip smem)"));
     build_items(b, 32);

@@ -15,8 +15,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
-#include "step_tma.cuh"
-#include "step_warp.cuh"
+#include "ring.cuh"
 #include "step_pair.cuh"
 #include "step_ext.cuh"
 #include "thermo.h"
@@ -36,53 +35,30 @@ int cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
     } while (0)
 
-#ifndef LBM_TXF
-#define LBM_TXF 256
-#endif
-#ifndef LBM_TMA_STAGES
-#define LBM_TMA_STAGES 6
-#endif
-constexpr int kTXf = LBM_TXF;  // columns per CTA, FP32
+constexpr int kTXf = 256;  // columns per CTA of the FP32 direct-load kernels
 constexpr int kTXd = 64;   // columns per CTA, FP64
 constexpr int kWallBandPP = 2;  // rows next to each wall that a periodic step gets wrong
 constexpr int kWallBandFE = 3;
 constexpr int kGraphSteps = 64;
 constexpr int kRedBlocks = 304;  // observables partial-reduction blocks (2 x 152 SMs)
-constexpr int kTmaStages = LBM_TMA_STAGES;  // row-pipeline depth of the TMA-fed FP32 kernels
-// Pseudopotential FP32 step: warp-independent windows (1) or CTA-synchronised strips (0).
-#ifndef LBM_PP_WARP
-#define LBM_PP_WARP 1
-#endif
-#ifndef LBM_PPW_STAGES
-#define LBM_PPW_STAGES 6
-#endif
-constexpr bool kPPWarp = LBM_PP_WARP != 0;
-constexpr int kPPWarps = 8;                    // consumer warps per CTA
-constexpr int kPPWStages = LBM_PPW_STAGES;
-using PPWSmem = lbmk::WarpStripSmem<kPPWarps, kPPWStages, 30>;
-constexpr int kPPWTX = PPWSmem::TX;            // widest strip (240 columns)
-// Pseudopotential FP32 step with two cells per lane (1; takes precedence over LBM_PP_WARP).
-#ifndef LBM_PP_PAIR
-#define LBM_PP_PAIR 1
-#endif
+// FP32 strip kernels (two cells per lane in warp windows fed by the row ring).  A consumer warp
+// reads staged rows q-2 .. q+1 (pseudopotential) or q-3 .. q+1 (free energy) while the producer
+// fills the next row, so the rings need at least 4 and 5 stages; fewer would leave the
+// producer waiting on a stage that is never released.
 #ifndef LBM_PPP_STAGES
 #define LBM_PPP_STAGES 6
-#endif
-constexpr bool kPPPair = LBM_PP_PAIR != 0;
-constexpr int kPPPWarps = 4;
-constexpr int kPPPStages = LBM_PPP_STAGES;     // >= 4: a warp reads rows q-2 .. q+1
-using PPPSmem = lbmk::WarpStripSmem<kPPPWarps, kPPPStages, 60>;
-constexpr int kPPPTX = PPPSmem::TX;
-// Free-energy FP32 step: two cells per lane in warp windows (1) or CTA-synchronised strips (0).
-#ifndef LBM_FE_PAIR
-#define LBM_FE_PAIR 1
 #endif
 #ifndef LBM_FEP_STAGES
 #define LBM_FEP_STAGES 6
 #endif
-constexpr bool kFEPair = LBM_FE_PAIR != 0;
+constexpr int kPPPWarps = 4;
+constexpr int kPPPStages = LBM_PPP_STAGES;
+static_assert(kPPPStages >= 4, "the pseudopotential strip ring needs at least 4 stages");
+using PPPSmem = lbmk::WarpStripSmem<kPPPWarps, kPPPStages, 60>;
+constexpr int kPPPTX = PPPSmem::TX;
 constexpr int kFEPWarps = 4;                   // consumer warps per CTA
-constexpr int kFEPStages = LBM_FEP_STAGES;     // >= 5: a warp reads rows q-3 .. q+1
+constexpr int kFEPStages = LBM_FEP_STAGES;
+static_assert(kFEPStages >= 5, "the free-energy strip ring needs at least 5 stages");
 using FEPSmem = lbmk::WarpStripSmem<kFEPWarps, kFEPStages, 60>;
 constexpr int kFEPTX = FEPSmem::TX;            // widest strip (240 columns)
 
@@ -316,11 +292,18 @@ static long long plane_pitch(int nx, int ny) {
     return (n + 63) / 64 * 64;  // 256-byte aligned planes for FP32, 512 for FP64
 }
 
+// Planes of one population buffer: the 9 populations, plus for FP32 the int16 plane that
+// extends the free-energy model's rest population (lbmk::rest_update).
+static size_t buffer_bytes(int precision, int nx, int ny) {
+    const size_t esz = precision == LBM_F64 ? 8 : 4;
+    return align256((precision == LBM_F64 ? 9 : 10) * (size_t)plane_pitch(nx, ny) * esz);
+}
+
 extern "C" size_t lbm_workspace_bytes(int precision, int nx, int ny) {
     if (nx < 1 || ny < 1) return 0;
     const size_t esz = precision == LBM_F64 ? 8 : 4;
     const size_t n = (size_t)nx * ny;
-    const size_t fbytes = align256(9 * (size_t)plane_pitch(nx, ny) * esz);
+    const size_t fbytes = buffer_bytes(precision, nx, ny);
     const size_t fields = align256(4 * n * esz);
     // ... + the one-sided walls' row solve (14 nx reals)
     return 2 * fbytes + fields + align256(kRedBlocks * 3 * sizeof(double)) + align256(8 * sizeof(double)) + 256 +
@@ -410,10 +393,8 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     {
         const bool ppm = p->model == LBM_PSEUDOPOTENTIAL;
         const bool fast = c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 2 * kWallBandFE &&
-                          kPPPair && kFEPair && std::getenv("LBM_NO_TMA") == nullptr;
-        const int tx = c->prec == LBM_F64 ? kTXd
-                       : (walls && !fast) ? kTXf
-                       : ppm ? (kPPPair ? kPPPTX : kPPWarp ? kPPWTX : kTXf) : (kFEPair ? kFEPTX : kTXf);
+                          std::getenv("LBM_NO_TMA") == nullptr;
+        const int tx = c->prec == LBM_F64 ? kTXd : (walls && !fast) ? kTXf : ppm ? kPPPTX : kFEPTX;
         c->rows = choose_rows(nx, ny, tx, ppm ? 16 : 12);
     }
     const size_t need = lbm_workspace_bytes(c->prec, nx, ny);
@@ -432,7 +413,7 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
         }
         c->own_ws = true;
     }
-    const size_t fbytes = align256(9 * (size_t)c->pitch * c->esz);
+    const size_t fbytes = buffer_bytes(c->prec, nx, ny);
     const size_t n = (size_t)nx * ny;
     c->f[0] = c->ws;
     c->f[1] = c->ws + fbytes;
@@ -444,7 +425,8 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->walls = walls;
     c->onesided = bc_y == LBM_BC_WALL_ZOUHE_ONESIDED && p->model == LBM_FREE_ENERGY;
     // walls: the periodic strip kernels serve the interior when both wall bands fit
-    c->use_tma = (!walls || (kPPPair && kFEPair && ny >= 2 * kWallBandFE)) && c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 4 && std::getenv("LBM_NO_TMA") == nullptr;
+    c->use_tma = (!walls || ny >= 2 * kWallBandFE) && c->prec == LBM_F32 && nx % 4 == 0 && nx >= 8 && ny >= 4 &&
+                 std::getenv("LBM_NO_TMA") == nullptr;
     cudaError_t e = cudaMallocHost(&c->h_pinned, 8 * sizeof(double));
     if (e != cudaSuccess) {
         if (c->own_ws) cudaFree(c->ws);
@@ -475,27 +457,14 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     fill_step_params(c->spf, c);
     fill_step_params(c->spd, c);
     if (c->use_tma) {
-        // the stage rings of wide tiles exceed the default 48 KB of dynamic shared memory
-        cudaError_t e1 = cudaFuncSetAttribute(lbmk::pp_step_tma<kTXf, kTmaStages>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)sizeof(lbmk::PPTmaSmem<kTXf, kTmaStages>));
-        cudaError_t e2 = cudaFuncSetAttribute(lbmk::fe_step_tma<kTXf, kTmaStages>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)sizeof(lbmk::FETmaSmem<kTXf, kTmaStages>));
-        cudaError_t e3 = cudaFuncSetAttribute(lbmk::pp_step_warp<kPPWarps, kPPWStages>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPWSmem));
-        cudaError_t e4 = cudaFuncSetAttribute(lbmk::fe_step_pair<kFEPWarps, kFEPStages>,
+        // the stage rings exceed the default 48 KB of dynamic shared memory
+        cudaError_t e1 = cudaFuncSetAttribute(lbmk::fe_step_pair<kFEPWarps, kFEPStages>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FEPSmem));
-        cudaError_t e5 = cudaFuncSetAttribute(lbmk::pp_step_pair<kPPPWarps, kPPPStages>,
+        cudaError_t e2 = cudaFuncSetAttribute(lbmk::pp_step_pair<kPPPWarps, kPPPStages>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPPSmem));
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess) {
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
             lbm_destroy(c);
-            const cudaError_t e = e1 != cudaSuccess   ? e1
-                                  : e2 != cudaSuccess ? e2
-                                  : e3 != cudaSuccess ? e3
-                                  : e4 != cudaSuccess ? e4
-                                                      : e5;
-            return cuda_fail(e, "cudaFuncSetAttribute(max dynamic smem)");
+            return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaFuncSetAttribute(max dynamic smem)");
         }
     }
     *out = c;
@@ -678,28 +647,14 @@ static int launch_step(lbm_ctx* c, int src, bool driven = false) {
                     (const double*)fin, (double*)fout, c->spd, 0, no_drive<double>(),
                     launch_wall_solve<double>(c, src, c->spd));
         }
-    } else if (c->use_tma && pp && kPPPair) {
+    } else if (c->use_tma && pp) {
         dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
         lbmk::pp_step_pair<kPPPWarps, kPPPStages><<<grid, (kPPPWarps + 1) * 32, sizeof(PPPSmem), c->stream>>>(
             (const float*)fin, (float*)fout, c->spf, c->d_err);
-    } else if (c->use_tma && pp && kPPWarp) {
-        dim3 grid((c->nx + kPPWTX - 1) / kPPWTX, (c->ny + c->rows - 1) / c->rows);
-        lbmk::pp_step_warp<kPPWarps, kPPWStages><<<grid, (kPPWarps + 1) * 32, sizeof(PPWSmem), c->stream>>>(
-            (const float*)fin, (float*)fout, c->spf, c->d_err);
-    } else if (c->use_tma && !pp && kFEPair) {
+    } else if (c->use_tma) {
         dim3 grid((c->nx + kFEPTX - 1) / kFEPTX, (c->ny + c->rows - 1) / c->rows);
         lbmk::fe_step_pair<kFEPWarps, kFEPStages><<<grid, (kFEPWarps + 1) * 32, sizeof(FEPSmem), c->stream>>>(
             (const float*)fin, (float*)fout, c->spf, c->d_err);
-    } else if (c->use_tma) {
-        dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
-        if (pp)
-            lbmk::pp_step_tma<kTXf, kTmaStages>
-                <<<grid, kTXf + 32, sizeof(lbmk::PPTmaSmem<kTXf, kTmaStages>), c->stream>>>(
-                    (const float*)fin, (float*)fout, c->spf, c->d_err);
-        else
-            lbmk::fe_step_tma<kTXf, kTmaStages>
-                <<<grid, kTXf + 32, sizeof(lbmk::FETmaSmem<kTXf, kTmaStages>), c->stream>>>(
-                    (const float*)fin, (float*)fout, c->spf, c->d_err);
     } else if (c->prec == LBM_F32) {
         dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
         if (pp)
@@ -865,6 +820,25 @@ static inline size_t shifted(int x, int y, int i, int nx, int ny) {
     return (size_t)ys * nx + xs;
 }
 
+// Host view of the compensated rest population of FP32 free-energy buffers (see
+// lbmk::rest_update): f_0 = hi + q 2^-16 ulp(hi).
+static bool has_rest_plane(const lbm_ctx* c) { return c->prec == LBM_F32 && c->prm.model == LBM_FREE_ENERGY; }
+static int float_exponent_bits(float hi) {
+    uint32_t b;
+    std::memcpy(&b, &hi, 4);
+    return (int)((b >> 23) & 0xff);
+}
+static double rest_decode(float hi, short q) {
+    const int e = float_exponent_bits(hi);
+    return (double)hi + (e > 39 ? std::ldexp((double)q, e - 166) : 0.0);
+}
+static short rest_encode_host(double v, float hi) {
+    const int e = float_exponent_bits(hi);
+    if (e <= 39) return 0;
+    const double q = std::nearbyint(std::ldexp(v - (double)hi, 166 - e));
+    return (short)std::max(-32767.0, std::min(32767.0, q));
+}
+
 extern "C" int lbm_set_populations(lbm_ctx* c, const double* f) {
     if (!c || !f) return LBM_ERR_ARG;
     const size_t n = (size_t)c->nx * c->ny;
@@ -881,6 +855,14 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f) {
                     reinterpret_cast<double*>(stage.data())[k] = v;
             }
         CK(cudaMemcpy(static_cast<char*>(c->f[0]) + (size_t)i * c->pitch * c->esz, stage.data(), n * c->esz,
+                      cudaMemcpyHostToDevice));
+    }
+    if (c->prec == LBM_F32) {
+        // rest-population extension: the part of f_0 below FP32 (free energy), else zero
+        std::vector<short> q(n, 0);
+        if (has_rest_plane(c))
+            for (size_t k = 0; k < n; ++k) q[k] = rest_encode_host(f[k], (float)f[k]);
+        CK(cudaMemcpy(static_cast<char*>(c->f[0]) + (size_t)9 * c->pitch * 4, q.data(), n * sizeof(short),
                       cudaMemcpyHostToDevice));
     }
     CK(cudaMemset(c->d_err, 0, sizeof(int)));
@@ -919,6 +901,12 @@ extern "C" int lbm_get_populations(lbm_ctx* c, double* f) {
                 f[i * n + shifted(x, y, i, c->nx, c->ny)] = v;
             }
     }
+    if (has_rest_plane(c)) {
+        std::vector<short> q(n);
+        CK(cudaMemcpy(q.data(), static_cast<char*>(c->f[c->cur]) + (size_t)9 * c->pitch * 4, n * sizeof(short),
+                      cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < n; ++k) f[k] = rest_decode((float)f[k], q[k]);
+    }
     return LBM_OK;
 }
 
@@ -938,6 +926,12 @@ extern "C" int lbm_get_populations_at(lbm_ctx* c, int n, const int* xs, const in
                 float v;
                 CK(cudaMemcpy(&v, static_cast<char*>(c->f[c->cur]) + off, 4, cudaMemcpyDeviceToHost));
                 out[9 * k + i] = v;
+                if (i == 0 && has_rest_plane(c)) {
+                    short q;
+                    const size_t qoff = (size_t)9 * c->pitch * 4 + ((size_t)ys_ * c->nx + xs_) * sizeof(short);
+                    CK(cudaMemcpy(&q, static_cast<char*>(c->f[c->cur]) + qoff, sizeof(short), cudaMemcpyDeviceToHost));
+                    out[9 * k] = rest_decode(v, q);
+                }
             } else {
                 CK(cudaMemcpy(&out[9 * k + i], static_cast<char*>(c->f[c->cur]) + off, 8, cudaMemcpyDeviceToHost));
             }
@@ -1146,7 +1140,17 @@ extern "C" int lbm_load(lbm_ctx* c, const char* path) {
     bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMCKPT1", 8) == 0 &&
               std::fread(hdr, sizeof(int), 4, fp) == 4 && std::fread(&step, sizeof(long long), 1, fp) == 1 &&
               std::fread(&prm, sizeof(lbm_params), 1, fp) == 1;
-    if (ok && (hdr[0] != c->nx || hdr[1] != c->ny || hdr[2] != c->prm.model || hdr[3] != c->prec)) {
+    // the checkpoint continues the run it was written from: same lattice, model, precision and
+    // resolved parameters (a state of one temperature or EOS is not a state of another)
+    const double saved[] = {prm.a, prm.b, prm.R, prm.Tr, prm.tau_nu, prm.tau_e, prm.tau_zeta, prm.tau_q,
+                            prm.tau_j, prm.kappa_P, prm.kappa_Li, prm.sigma_Li, prm.kappa, prm.A,
+                            prm.body_fx, prm.body_fy};
+    const double mine[] = {c->prm.a, c->prm.b, c->prm.R, c->prm.Tr, c->prm.tau_nu, c->prm.tau_e,
+                           c->prm.tau_zeta, c->prm.tau_q, c->prm.tau_j, c->prm.kappa_P, c->prm.kappa_Li,
+                           c->prm.sigma_Li, c->prm.kappa, c->prm.A, c->prm.body_fx, c->prm.body_fy};
+    bool same = true;
+    for (size_t k = 0; k < sizeof(saved) / sizeof(saved[0]); ++k) same = same && saved[k] == mine[k];
+    if (ok && (hdr[0] != c->nx || hdr[1] != c->ny || hdr[2] != c->prm.model || hdr[3] != c->prec || !same)) {
         std::fclose(fp);
         return LBM_ERR_ARG;
     }

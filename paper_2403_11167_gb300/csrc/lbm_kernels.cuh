@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbmk {
 
 // D2Q9, Eq. (2): 0 rest; 1 (1,0); 2 (0,1); 3 (-1,0); 4 (0,-1); 5 (1,1); 6 (-1,1); 7 (-1,-1); 8 (1,-1).
@@ -102,15 +104,20 @@ __device__ __forceinline__ void pull9(const real* __restrict__ f, long long pitc
     v[8] = __ldg(f + 8 * pitch + op + xm);
 }
 
+// rho = sum_i f_i (Eq. 6a), summed in mirror pairs (1,3), (2,4), (5,7), (6,8): reflecting the
+// lattice in x or in y (or transposing it) maps every partial sum onto itself, so mirror-image
+// cells get bitwise equal densities and a mirror-symmetric state stays symmetric in FP32.
 template <typename real>
 __device__ __forceinline__ real sum9(const real v[9]) {
-    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+    return v[0] + (((v[1] + v[3]) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8])));
 }
 
 // f* = f + M^-1 dm for the moment increments dm (rho increment is zero); M^-1 of Eq. (S49).
+// d0: if not null, receives the rest population's increment, and v[0] is left unchanged (the
+// caller applies it to a compensated rest population; see rest_update).
 template <typename real>
 __device__ __forceinline__ void apply_dm(real v[9], real de, real dz, real djx, real dqx, real djy, real dqy,
-                                         real dpxx, real dpxy) {
+                                         real dpxx, real dpxy, real* d0 = nullptr) {
     const real A = -de * real(1.0 / 36.0) - dz * real(1.0 / 18.0);
     const real B = de * real(1.0 / 18.0) + dz * real(1.0 / 36.0);
     const real X1 = (djx - dqx) * real(1.0 / 6.0);
@@ -119,7 +126,10 @@ __device__ __forceinline__ void apply_dm(real v[9], real de, real dz, real djx, 
     const real Y2 = djy * real(1.0 / 6.0) + dqy * real(1.0 / 12.0);
     const real Pp = dpxx * real(0.25);
     const real Z = dpxy * real(0.25);
-    v[0] += (dz - de) * real(1.0 / 9.0);
+    if (d0)
+        *d0 = (dz - de) * real(1.0 / 9.0);
+    else
+        v[0] += (dz - de) * real(1.0 / 9.0);
     v[1] += A + X1 + Pp;
     v[2] += A + Y1 - Pp;
     v[3] += A - X1 + Pp;
@@ -241,11 +251,28 @@ __device__ __forceinline__ real fe_mu(real rc, const real rn[9], const StepParam
 }
 
 // ---------------------------------------------------------------------------------
-// FP32 free-energy arithmetic, written once for one cell (F1) or two cells at a time (F2,
+// FP32 arithmetic of both models, written once for one cell (F1) or two cells at a time (F2,
 // Blackwell's packed FP32: one instruction computes both lanes).  Every operation is an
 // explicit correctly rounded add / multiply / fused multiply-add, never re-associated or
 // contracted by the compiler, so the single-cell and the two-cell kernels produce bitwise
-// identical cells.  The algebra is that of fe_collide / fe_mu above (Eqs. 20, 21, 24, 29).
+// identical cells.  The algebra is that of pp_collide / fe_collide / fe_mu above (Eqs. 10-13,
+// 20, 21, 24, 29-32), arranged for FP32 in three ways:
+//  * Mirror equivariance.  Every sum over velocities is grouped so that reflecting the lattice
+//    in x (1<->3, 5<->6, 7<->8) or in y (2<->4, 5<->8, 6<->7) maps each partial result onto
+//    itself or onto its exact negative (IEEE addition is commutative and a - b = -(b - a)).
+//    A mirror-symmetric state therefore stays bitwise symmetric: its momentum is exactly zero
+//    and a static droplet or slab cannot drift rigidly from rounding (in FP32 it otherwise
+//    wanders by ~1e-5 cells per 1e4 steps).
+//  * Scale-exact constants.  c_s^2 = 1/3 and the stencil weights 1/3, 1/12 round up by 3e-8 in
+//    FP32.  In the pseudopotential model the lattice pressure rho c_s^2 must cancel the rho c_s^2
+//    inside psi^2 (Eq. 11) against a force of exactly the stencil's scale, so these roundings act
+//    as a spurious -3e-8 rho term in the equation of state (a 1.6e-6 relative change of the
+//    temperature at Tr = 0.8, shifting the vapour density by ~1e-5).  psi^2 therefore uses 1/3
+//    as a hi + lo pair, the force stencil integer weights times a hi + lo 1/12, and the
+//    momentum increments of M^-1 are formed so that they sum to the force up to one rounding.
+//  * No rest population in small differences.  In the free-energy model f_0 = rho carries
+//    almost all of the mass, so e - e^eq and zeta - zeta^eq are formed from the moving
+//    populations alone (rho = f_0 + sum of the others substituted exactly).
 struct F1 {
     float v;
     __device__ __forceinline__ F1() {}
@@ -295,28 +322,64 @@ __device__ __forceinline__ F2 rcp_v(F2 x) { return F2(__frcp_rn(x.v.x), __frcp_r
 
 template <class F>
 __device__ __forceinline__ F sum9_v(const F v[9]) {
-    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+    return v[0] + (((v[1] + v[3]) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8])));
 }
+
+// 1/3 and 1/12 as FP32 hi + lo pairs (hi the rounded value, lo the rounded remainder; the pair
+// is exact to 3e-16).
+constexpr float kThirdHi = 0x1.555556p-2f, kThirdLo = -0x1.555556p-27f;
+constexpr float kTwelfthHi = 0x1.555556p-4f, kTwelfthLo = -0x1.555556p-29f;
+
+// Sums over the lattice velocities in mirror-equivariant grouping (see above).
+//   jx = f1 - f3 + f5 - f6 - f7 + f8, jy = f2 - f4 + f5 + f6 - f7 - f8, sax = f1 + f2 + f3 + f4.
+template <class F>
+__device__ __forceinline__ F mom_jx(const F v[9]) { return (v[1] - v[3]) + ((v[5] - v[6]) + (v[8] - v[7])); }
+template <class F>
+__device__ __forceinline__ F mom_jy(const F v[9]) { return (v[2] - v[4]) + ((v[5] - v[8]) + (v[6] - v[7])); }
+template <class F>
+__device__ __forceinline__ F sum_axes(const F v[9]) { return (v[1] + v[3]) + (v[2] + v[4]); }
+
+// 12 sum_i omega_i phi(x + c_i) c_i with omega = 1/3 (axes), 1/12 (diagonals): integer weights,
+// exact up to the rounding of the last operation.
+template <class F>
+__device__ __forceinline__ F stencil12_x(const F n[9]) {
+    return fmav(F::c(4.0f), n[1] - n[3], (n[5] - n[7]) + (n[8] - n[6]));
+}
+template <class F>
+__device__ __forceinline__ F stencil12_y(const F n[9]) {
+    return fmav(F::c(4.0f), n[2] - n[4], (n[5] - n[7]) + (n[6] - n[8]));
+}
+template <class F>
+__device__ __forceinline__ F div12(F t) { return fmav(t, F::c(kTwelfthHi), t * F::c(kTwelfthLo)); }
 
 // mu at the cell from rho at the cell (rc) and at x + c_i (rn[1..8]).
 template <class F>
 __device__ __forceinline__ F fe_mu_v(F rc, const F rn[9], const StepParams<float>& P) {
-    const F lap = fmav((rn[1] - rc) + (rn[2] - rc) + ((rn[3] - rc) + (rn[4] - rc)), F::c(2.0f / 3.0f),
+    const F lap = fmav(((rn[1] - rc) + (rn[3] - rc)) + ((rn[2] - rc) + (rn[4] - rc)), F::c(2.0f / 3.0f),
                        ((rn[5] - rc) + (rn[6] - rc) + ((rn[7] - rc) + (rn[8] - rc))) * F::c(1.0f / 6.0f));
     return fmav(F::c(-P.kappa), lap, mu_bulk_v(rc, P));
 }
 
-template <class F>
-__device__ __forceinline__ void apply_dm_v(F v[9], F de, F dz, F djx, F dqx, F djy, F dqy, F dpxx, F dpxy) {
+// f* = f + M^-1 dm (Eq. S49) in the FP32 arithmetic.  COMP: the rest population's increment
+// goes to *d0 and v[0] is left unchanged (compensated rest population, see rest_update).
+template <class F, bool COMP = false>
+__device__ __forceinline__ void apply_dm_v(F v[9], F de, F dz, F djx, F dqx, F djy, F dqy, F dpxx, F dpxy,
+                                           F* d0 = nullptr) {
     const F A = fmav(de, F::c(-1.0f / 36.0f), dz * F::c(-1.0f / 18.0f));
     const F B = fmav(de, F::c(1.0f / 18.0f), dz * F::c(1.0f / 36.0f));
     const F X1 = (djx - dqx) * F::c(1.0f / 6.0f);
     const F Y1 = (djy - dqy) * F::c(1.0f / 6.0f);
-    const F X2 = fmav(djx, F::c(1.0f / 6.0f), dqx * F::c(1.0f / 12.0f));
-    const F Y2 = fmav(djy, F::c(1.0f / 6.0f), dqy * F::c(1.0f / 12.0f));
+    // X2 = djx / 6 + dqx / 12 taken as (djx - 2 X1) / 4, so that 2 X1 + 4 X2 (the x momentum
+    // added to the populations) equals djx up to one rounding, without the 3e-8 scale error of a
+    // rounded 1/6
+    const F X2 = fmav(F::c(-2.0f), X1, djx) * F::c(0.25f);
+    const F Y2 = fmav(F::c(-2.0f), Y1, djy) * F::c(0.25f);
     const F Pp = dpxx * F::c(0.25f);
     const F Z = dpxy * F::c(0.25f);
-    v[0] = fmav(dz - de, F::c(1.0f / 9.0f), v[0]);
+    if constexpr (COMP)
+        *d0 = (dz - de) * F::c(1.0f / 9.0f);
+    else
+        v[0] = fmav(dz - de, F::c(1.0f / 9.0f), v[0]);
     v[1] = v[1] + ((A + X1) + Pp);
     v[2] = v[2] + ((A + Y1) - Pp);
     v[3] = v[3] + ((A - X1) + Pp);
@@ -328,25 +391,23 @@ __device__ __forceinline__ void apply_dm_v(F v[9], F de, F dz, F djx, F dqx, F d
 }
 
 // Improved well-balanced free-energy collision (Eqs. 1, 6, 20, 21, 24); mn, rn: mu and rho
-// at x + c_i (i = 1..8).
-template <class F>
+// at x + c_i (i = 1..8).  COMP: the rest population's increment goes to *d0, v[0] unchanged.
+template <class F, bool COMP = false>
 __device__ __forceinline__ void fe_collide_v(F v[9], F rho, const F mn[9], const F rn[9],
-                                             const StepParams<float>& P) {
+                                             const StepParams<float>& P, F* d0 = nullptr) {
     const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
     const F gmx = fmav(mn[1] - mn[3], w1, ((mn[5] - mn[7]) + (mn[8] - mn[6])) * w2);
     const F gmy = fmav(mn[2] - mn[4], w1, ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2);
     const F grx = fmav(rn[1] - rn[3], w1, ((rn[5] - rn[7]) + (rn[8] - rn[6])) * w2);
     const F gry = fmav(rn[2] - rn[4], w1, ((rn[5] - rn[7]) + (rn[6] - rn[8])) * w2);
     const F Fx = fmav(-rho, gmx, F::c(P.fx)), Fy = fmav(-rho, gmy, F::c(P.fy));
-    const F jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
-    const F jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const F jx = mom_jx(v);
+    const F jy = mom_jy(v);
     const F inv_rho = rcp_v(rho);
     const F ux = fmav(F::c(0.5f), Fx, jx) * inv_rho;
     const F uy = fmav(F::c(0.5f), Fy, jy) * inv_rho;
-    const F sax = (v[1] + v[2]) + (v[3] + v[4]);
+    const F sax = sum_axes(v);
     const F sdg = (v[5] + v[6]) + (v[7] + v[8]);
-    const F e = fmav(F::c(-4.0f), v[0], fmav(F::c(2.0f), sdg, -sax));
-    const F z = fmav(F::c(4.0f), v[0], fmav(F::c(-2.0f), sax, sdg));
     const F qx = fmav(F::c(2.0f), v[3] - v[1], (v[5] - v[6]) + (v[8] - v[7]));
     const F qy = fmav(F::c(2.0f), v[4] - v[2], (v[5] + v[6]) - (v[7] + v[8]));
     const F pxx = (v[1] + v[3]) - (v[2] + v[4]);
@@ -358,13 +419,18 @@ __device__ __forceinline__ void fe_collide_v(F v[9], F rho, const F mn[9], const
     const F fe = fmav(F::c(6.0f), uF, F::c(4.0f) * s);
     const float he = 1.0f - 0.5f * P.s_e, hz = 1.0f - 0.5f * P.s_z, hq = 1.0f - 0.5f * P.s_q,
                 hn = 1.0f - 0.5f * P.s_nu;
-    const F de = fmav(F::c(he), fe, F::c(-P.s_e) * (e - rho * fmav(F::c(3.0f), uu, F::c(-4.0f))));
-    const F dz = fmav(F::c(-hz), fe, F::c(-P.s_z) * (z - rho * fmav(F::c(-3.0f), uu, F::c(4.0f))));
+    // e - e^eq = (-4 f0 - sax + 2 sdg) - rho (3 uu - 4) and zeta - zeta^eq = (4 f0 - 2 sax + sdg)
+    // - rho (4 - 3 uu) with rho = f0 + sax + sdg: f0 cancels exactly
+    const F rhouu = F::c(3.0f) * rho * uu;
+    const F ene = fmav(F::c(3.0f), sax, fmav(F::c(6.0f), sdg, -rhouu));
+    const F zne = fmav(F::c(-6.0f), sax, fmav(F::c(-3.0f), sdg, rhouu));
+    const F de = fmav(F::c(he), fe, F::c(-P.s_e) * ene);
+    const F dz = fmav(F::c(-hz), fe, F::c(-P.s_z) * zne);
     const F dqx = fmav(F::c(-hq), Fx, F::c(-P.s_q) * fmav(rho, ux, qx));
     const F dqy = fmav(F::c(-hq), Fy, F::c(-P.s_q) * fmav(rho, uy, qy));
     const F dpxx = fmav(F::c(2.0f * hn), fmav(ux, Gx, -(uy * Gy)), F::c(-P.s_nu) * (pxx - rho * fmav(ux, ux, -(uy * uy))));
     const F dpxy = fmav(F::c(hn), fmav(ux, Gy, uy * Gx), F::c(-P.s_nu) * (pxy - rho * ux * uy));
-    apply_dm_v(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+    apply_dm_v<F, COMP>(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy, d0);
 }
 
 // Carnahan-Starling pressure (Eq. 28) and pseudopotential (Eq. 11, G = -1), explicit ops.
@@ -379,7 +445,8 @@ __device__ __forceinline__ F1 sqrt_v(F1 x) { return F1(__fsqrt_rn(x.v)); }
 __device__ __forceinline__ F2 sqrt_v(F2 x) { return F2(__fsqrt_rn(x.v.x), __fsqrt_rn(x.v.y)); }
 template <class F>
 __device__ __forceinline__ F pseudo_psi_v(F rho, const StepParams<float>& P) {
-    return sqrt_v(F::c(2.0f) * fmav(rho, F::c(1.0f / 3.0f), -cs_pressure_v(rho, P)));
+    // rho c_s^2 - p with c_s^2 = 1/3 as a hi + lo pair (scale-exact; see above)
+    return sqrt_v(F::c(2.0f) * fmav(rho, F::c(kThirdHi), fmav(rho, F::c(kThirdLo), -cs_pressure_v(rho, P))));
 }
 
 // Modified pseudopotential collision (Eqs. 1, 4, 6, 10, 13, 30-32) in the algebra of pp_collide:
@@ -387,8 +454,8 @@ __device__ __forceinline__ F pseudo_psi_v(F rho, const StepParams<float>& P) {
 template <class F>
 __device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9], const StepParams<float>& P) {
     const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
-    const F Sx = fmav(pn[1] - pn[3], w1, ((pn[5] - pn[7]) + (pn[8] - pn[6])) * w2);
-    const F Sy = fmav(pn[2] - pn[4], w1, ((pn[5] - pn[7]) + (pn[6] - pn[8])) * w2);
+    const F Sx = div12(stencil12_x(pn));
+    const F Sy = div12(stencil12_y(pn));
     const F Fx = fmav(pc, Sx, F::c(P.fx)), Fy = fmav(pc, Sy, F::c(P.fy));
     const F d1 = pn[1] - pc, d2 = pn[2] - pc, d3 = pn[3] - pc, d4 = pn[4] - pc;
     const F d5 = pn[5] - pc, d6 = pn[6] - pc, d7 = pn[7] - pc, d8 = pn[8] - pc;
@@ -401,12 +468,12 @@ __device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9],
     const F Qyy = pc * fmav(F::c(P.kA), sa, F::c(P.kB) * syy);
     const F Qxy = pc * (F::c(P.kB) * sxy);
     const F L = F::c(P.li) * fmav(Sx, Sx, Sy * Sy);
-    const F jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
-    const F jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const F jx = mom_jx(v);
+    const F jy = mom_jy(v);
     const F inv_rho = rcp_v(rho);
     const F ux = fmav(F::c(0.5f), Fx, jx) * inv_rho;
     const F uy = fmav(F::c(0.5f), Fy, jy) * inv_rho;
-    const F sax = (v[1] + v[2]) + (v[3] + v[4]);
+    const F sax = sum_axes(v);
     const F sdg = (v[5] + v[6]) + (v[7] + v[8]);
     const F e = fmav(F::c(-4.0f), v[0], fmav(F::c(2.0f), sdg, -sax));
     const F z = fmav(F::c(4.0f), v[0], fmav(F::c(-2.0f), sax, sdg));
@@ -429,6 +496,69 @@ __device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9],
     const F dpxy = fmav(F::c(hn), fmav(ux, Fy, uy * Fx), F::c(-P.s_nu) * ((pxy - rho * ux * uy) + Qxy));
     // j* - j = F exactly (tau_j drops out)
     apply_dm_v(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+}
+
+// ---------------------------------------------------------------------------------
+// Compensated rest population of the FP32 free-energy model.
+//
+// In the free-energy model the rest population carries almost all of a cell's mass (f_0 = rho
+// at rest, Eq. 20), so FP32 rounds the mass of every cell at ulp(rho) per step and the total
+// mass random-walks; the well-balanced scheme's neutral period-2 density mode and the droplet
+// radius follow (measured: 2e-5 .. 9e-5 relative density error after 1e4 static steps).  FP32
+// free-energy buffers therefore carry a tenth plane of int16 q per cell: the rest population
+// is hi + q 2^-16 ulp(hi), hi the FP32 value of plane 0 (about 40 significant bits).  Every
+// collision adds its rest increment d with an error-free transformation, so the stored mass
+// changes only by the rounding of the small moving populations.  The arithmetic of the step
+// reads hi only (rho = sum f_i in FP32); the observables and the host population views add q.
+
+// 2^-16 ulp(hi) and its inverse (0 for |hi| < 2^-87, where q is ignored).
+__device__ __forceinline__ float rest_lo_unit(float hi) {
+    const int e = (__float_as_int(hi) >> 23) & 0xff;
+    return e > 39 ? __int_as_float((e - 39) << 23) : 0.0f;
+}
+__device__ __forceinline__ float rest_lo_inv_unit(float hi) {
+    const int e = (__float_as_int(hi) >> 23) & 0xff;
+    return e > 39 ? __int_as_float((293 - e) << 23) : 0.0f;
+}
+
+// (hi + q 2^-16 ulp(hi)) + d -> (hi, q), exact up to 2^-17 ulp of the new hi: TwoSum of hi and
+// d, the old q carried in the error term, Fast2Sum renormalisation.
+__device__ __forceinline__ void rest_update(float& hi, int& q, float d) {
+    const float lo = __fmul_rn((float)q, rest_lo_unit(hi));
+    const float s = __fadd_rn(hi, d);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));  // hi + d = s + err
+    const float t = __fadd_rn(err, lo);
+    const float h2 = __fadd_rn(s, t);
+    const float l2 = __fsub_rn(t, __fsub_rn(h2, s));  // s + t = h2 + l2
+    const int qn = __float2int_rn(__fmul_rn(l2, rest_lo_inv_unit(h2)));
+    q = max(-32767, min(32767, qn));
+    hi = h2;
+}
+
+// The rest-population plane of an FP32 buffer (plane 9, int16).
+__device__ __forceinline__ short* rest_lo_plane(float* f, long long pitch) {
+    return reinterpret_cast<short*>(f + 9 * pitch);
+}
+__device__ __forceinline__ const short* rest_lo_plane(const float* f, long long pitch) {
+    return reinterpret_cast<const short*>(f + 9 * pitch);
+}
+
+// q of a value v given its FP32 rounding hi (0 when v carries no more than FP32).
+template <typename src_t>
+__device__ __forceinline__ short rest_encode(src_t v, float hi) {
+    if constexpr (std::is_same<src_t, double>::value) {
+        const double q = rint((v - (double)hi) * (double)rest_lo_inv_unit(hi));
+        return (short)fmax(-32767.0, fmin(32767.0, q));
+    } else {
+        return 0;
+    }
+}
+
+// rho of pulled FP32 free-energy populations including the rest population's extension q.
+__device__ __forceinline__ float sum9_rest(const float v[9], int q) {
+    return v[0] + ((((v[1] + v[3]) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8]))) +
+                   __fmul_rn((float)q, rest_lo_unit(v[0])));
 }
 
 // FP32 single-cell entry points used by every FP32 pseudopotential kernel (step, batch,
@@ -466,6 +596,24 @@ __device__ __forceinline__ void fe_collide(float v[9], float rho, const float mn
     fe_collide_v(vv, F1(rho), m, r, P);
 #pragma unroll
     for (int i = 0; i < 9; ++i) v[i] = vv[i].v;
+}
+// The same collision with a compensated rest population: v[0] (hi) and q of the cell are
+// updated together (see rest_update).
+__device__ __forceinline__ void fe_collide_comp(float v[9], int& q, float rho, const float mn[9], const float rn[9],
+                                                const StepParams<float>& P) {
+    F1 vv[9], m[9], r[9], d0;
+    m[0] = r[0] = F1(0.0f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) vv[i] = F1(v[i]);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        m[i] = F1(mn[i]);
+        r[i] = F1(rn[i]);
+    }
+    fe_collide_v<F1, true>(vv, F1(rho), m, r, P, &d0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) v[i] = vv[i].v;
+    rest_update(v[0], q, d0.v);
 }
 __device__ __forceinline__ float fe_mu(float rc, const float rn[9], const StepParams<float>& P) {
     // rn[0] is not used and callers need not set it
@@ -649,8 +797,14 @@ __global__ void __launch_bounds__(TX + 32) fe_step_kernel(const real* __restrict
             rn[1] = r0[rc + 1]; rn[2] = rp[rc]; rn[3] = r0[rc - 1]; rn[4] = rm[rc];
             rn[5] = rp[rc + 1]; rn[6] = rp[rc - 1]; rn[7] = rm[rc - 1]; rn[8] = rm[rc + 1];
             const real rho_c = r0[rc];
-            fe_collide(p0, rho_c, mn, rn, P);
             const long long o = (long long)(r - 2) * nx + x;
+            if constexpr (std::is_same<real, float>::value) {
+                int q = rest_lo_plane(fin, pitch)[o];  // compensated rest population
+                fe_collide_comp(p0, q, rho_c, mn, rn, P);
+                rest_lo_plane(fout, pitch)[o] = (short)q;
+            } else {
+                fe_collide(p0, rho_c, mn, rn, P);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
         }
@@ -723,6 +877,8 @@ __global__ void init_kernel(const src_t* __restrict__ rho0, real* __restrict__ S
             S[c] = (real)rho0[c];
 #pragma unroll
             for (int i = 1; i < 9; ++i) S[i * pitch + c] = real(0);
+            if constexpr (std::is_same<real, float>::value)
+                rest_lo_plane(S, pitch)[c] = rest_encode(rho0[c], S[c]);
         }
     }
 }
@@ -737,7 +893,11 @@ __global__ void rho_kernel(const real* __restrict__ f, real* __restrict__ rho, r
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         real v[9];
         pull_cell(f, P.pitch, (int)(c % P.nx), (int)(c / P.nx), P.nx, P.ny, v);
-        const real r = sum9(v);
+        real r;
+        if constexpr (std::is_same<real, float>::value)
+            r = model == 1 ? sum9_rest(v, rest_lo_plane(f, P.pitch)[c]) : sum9(v);
+        else
+            r = sum9(v);
         rho[c] = r;
         aux[c] = model == 0 ? pseudo_psi(r, P) : r;
     }

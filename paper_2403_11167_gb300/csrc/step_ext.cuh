@@ -388,11 +388,15 @@ __global__ void __launch_bounds__(TX + 32) fe_step_ext(const real* __restrict__ 
                 const real Fx = -rho_c * grad_x(mn) + P.fx;  // F = -rho grad mu + body force
                 wall_fill(p0, c != 0, real(-0.5) * Fx, real(-0.5) * Pc.fy);
             }
-            if (D.rho_ave)
-                fe_collide(p0, rho_c, mn, rn, with_drive(Pc, D, x, rho_c, s_rave));
-            else
-                fe_collide(p0, rho_c, mn, rn, Pc);
             const long long o = (long long)c * nx + x;
+            const StepParams<real> Pd = D.rho_ave ? with_drive(Pc, D, x, rho_c, s_rave) : Pc;
+            if constexpr (std::is_same<real, float>::value) {
+                int q = rest_lo_plane(fin, pitch)[o];  // compensated rest population
+                fe_collide_comp(p0, q, rho_c, mn, rn, Pd);
+                rest_lo_plane(fout, pitch)[o] = (short)q;
+            } else {
+                fe_collide(p0, rho_c, mn, rn, Pd);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
         }
@@ -440,7 +444,11 @@ __global__ void rho_walls_kernel(const real* __restrict__ f, real* __restrict__ 
         real v[9];
         pull_row_ext<true>(f, P, x, x == 0 ? P.nx - 1 : x - 1, x == P.nx - 1 ? 0 : x + 1, y, v, wjy);
         if (!wjy && E.on && E.g != real(0) && (y == 0 || y == P.ny - 1)) wall_gravity_refill(v, y != 0, P, E);
-        const real r = sum9(v);
+        real r;
+        if constexpr (std::is_same<real, float>::value)
+            r = model == 1 ? sum9_rest(v, rest_lo_plane(f, P.pitch)[c]) : sum9(v);
+        else
+            r = sum9(v);
         rho[c] = r;
         aux[c] = model == 0 ? pseudo_psi(r, P) : r;
     }
@@ -537,7 +545,7 @@ __global__ void velocity_ext_kernel(const real* __restrict__ f, const real* __re
 template <typename real>
 __device__ __forceinline__ void fe_collide_iwb(real v[9], real rho, const real mn[9], const real rn[9],
                                                const real uxn[9], const real uyn[9], real Fxe, real Fye, real pg,
-                                               const StepParams<real>& P, const Ext<real>& E) {
+                                               const StepParams<real>& P, const Ext<real>& E, real* d0 = nullptr) {
     const real w1 = real(1.0 / 3.0), w2 = real(1.0 / 12.0);
     const real gmx = grad_x(mn);
     const real gmy = (mn[2] - mn[4]) * w1 + ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2;
@@ -579,7 +587,7 @@ __device__ __forceinline__ void fe_collide_iwb(real v[9], real rho, const real m
     const real dqy = -P.s_q * (qy + rho * uy) - (real(1) - real(0.5) * P.s_q) * Fy;
     const real dpxx = -P.s_nu * (pxx - pxx_eq) + (real(1) - real(0.5) * P.s_nu) * real(2) * (ux * Gx - uy * Gy);
     const real dpxy = -P.s_nu * (pxy - pxy_eq) + (real(1) - real(0.5) * P.s_nu) * (ux * Gy + uy * Gx);
-    apply_dm(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+    apply_dm(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy, d0);
 }
 
 // One column per thread plus a halo warp whose lanes 0..5 hold the columns x0-3, x0-2, x0-1,
@@ -716,8 +724,17 @@ __global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ 
                 }
             }
             const real pg = E.on ? E.rho_g * E.g * (real(c) - E.y_ref) : real(0);
-            fe_collide_iwb(p0, rho_c, mn, rn, un, vn, ext_fx(rho_c), ext_fy(rho_c) + fy_w, pg, P, E);
             const long long o = (long long)c * nx + x;
+            if constexpr (std::is_same<real, float>::value) {
+                // compensated rest population
+                int q = rest_lo_plane(fin, pitch)[o];
+                float d0;
+                fe_collide_iwb(p0, rho_c, mn, rn, un, vn, ext_fx(rho_c), ext_fy(rho_c) + fy_w, pg, P, E, &d0);
+                rest_update(p0[0], q, d0);
+                rest_lo_plane(fout, pitch)[o] = (short)q;
+            } else {
+                fe_collide_iwb(p0, rho_c, mn, rn, un, vn, ext_fx(rho_c), ext_fy(rho_c) + fy_w, pg, P, E);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = p0[i];
         }
@@ -750,7 +767,10 @@ __global__ void init_iwb_kernel(const src_t* __restrict__ rho0, real* __restrict
             const int ys = (y + cys[i] + ny) % ny;
             const double pg = pg_coef * ((double)ys - y_ref);
             const double r = (double)rho0[shifted_cell(x, y, cxs[i], cys[i], nx, ny)];
-            S[i * pitch + c] = (real)(i == 0 ? r - (1.0 - w[0]) * 3.0 * pg : w[i] * 3.0 * pg);
+            const double f = i == 0 ? r - (1.0 - w[0]) * 3.0 * pg : w[i] * 3.0 * pg;
+            S[i * pitch + c] = (real)f;
+            if constexpr (std::is_same<real, float>::value)
+                if (i == 0) rest_lo_plane(S, pitch)[c] = rest_encode(f, (float)f);
         }
     }
 }

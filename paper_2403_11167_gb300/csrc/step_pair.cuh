@@ -3,7 +3,7 @@
 //
 // Per-cell arithmetic: fe_mu_v / fe_collide_v (lbm_kernels.cuh) on F2, Blackwell's packed
 // FP32, so one instruction updates both cells of a lane; results are bitwise those of the
-// single-cell kernels.  Data movement: the TMA row ring of step_warp.cuh (one producer warp,
+// single-cell kernels.  Data movement: the row ring of ring.cuh (one producer warp,
 // per-stage full/empty mbarriers, no CTA barrier per row).  Each consumer warp owns a run of
 // 60 columns (the last one fewer; warps beyond the strip stay idle) plus two halo columns on each side, two adjacent columns per lane: it keeps rho
 // of the last four rows and mu of the last three in registers, reads x-neighbours with warp
@@ -14,14 +14,17 @@
 // rows q-2..q; collide row q-2 with mu rows q-3..q-1 and rho rows q-3..q-1, re-pulling its
 // populations from staged rows q-3..q-1; release the stage of row q-3.
 //
+// The free-energy kernel also carries the compensated rest population (rest_update in
+// lbm_kernels.cuh): each lane reads and writes one 32-bit word of the int16 rest plane per
+// row (its two cells), loaded when the row is pulled and used two iterations later.
+//
 // Requirements (checked on the host): nx % 4 == 0, nx >= 8, ny >= 4; every wait bounded.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "lbm_kernels.cuh"
-#include "step_tma.cuh"
-#include "step_warp.cuh"
+#include "ring.cuh"
 
 namespace lbmk {
 
@@ -119,6 +122,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
     const int sc = col + 4;
     Row2 r1, r2, r3;  // rho of rows q-1, q-2, q-3
     Row2 m2, m3;      // mu of rows q-2, q-3
+    // rest-population extensions q (two int16 per lane) of rows q, q-1, q-2: loaded when row q
+    // is pulled, used two iterations later by its collision
+    const unsigned* qin = reinterpret_cast<const unsigned*>(rest_lo_plane(fin, P.pitch));
+    unsigned* qout = reinterpret_cast<unsigned*>(rest_lo_plane(fout, P.pitch));
+    unsigned ql0 = 0, ql1 = 0, ql2 = 0;
     r1.c = r2.c = r3.c = m2.c = m3.c = F2::c(1.0f);
     r1.L = r1.R = r2.L = r2.R = r3.L = r3.R = m2.L = m2.R = m3.L = m3.R = 1.0f;
     bool ok = mbar_wait_bounded(&sm.full[0], 0) && mbar_wait_bounded(&sm.full[1], 0);
@@ -127,6 +135,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
         const int k = q + 1 - rbase;  // ring index of row q+1
         ok = mbar_wait_bounded(&sm.full[k % S], (uint32_t)((k / S) & 1));
         if (!ok) break;
+        if (out && q >= y0 && q < y1) ql0 = __ldg(qin + (((long long)q * nx + x0 + col) >> 1));
         // pull row q, rho(q)
         F2 rho0 = F2::c(1.0f);
         if (act) {
@@ -149,10 +158,19 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
             pull_pair<W8>(sm.stage[(k - 4) % S], sm.stage[(k - 3) % S], sm.stage[(k - 2) % S], sc, v);
             neighbours_pair(m3, m2, m1, mn);
             neighbours_pair(r3, r2, r1, rn);
-            fe_collide_v(v, r2.c, mn, rn, P);
-            float* o = fout + (long long)(q - 2) * nx + x0 + col;
+            F2 d0;
+            fe_collide_v<F2, true>(v, r2.c, mn, rn, P, &d0);
+            // compensated rest population of both cells (rest_update)
+            int qa = (int)(short)(ql2 & 0xffffu), qb = (int)ql2 >> 16;
+            float ha = v[0].v.x, hb = v[0].v.y;
+            rest_update(ha, qa, d0.v.x);
+            rest_update(hb, qb, d0.v.y);
+            v[0] = F2(ha, hb);
+            const long long oc = (long long)(q - 2) * nx + x0 + col;
+            float* o = fout + oc;
 #pragma unroll
             for (int i = 0; i < 9; ++i) *reinterpret_cast<float2*>(o + i * P.pitch) = v[i].v;
+            qout[oc >> 1] = ((unsigned)qa & 0xffffu) | ((unsigned)qb << 16);
         }
         // row q-3 (ring index k-4) is no longer read by this warp
         __syncwarp();
@@ -162,6 +180,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
         r1 = r0;
         m3 = m2;
         m2 = m1;
+        ql2 = ql1;
+        ql1 = ql0;
     }
     if (!ok) atomicExch(err, 1);
 }

@@ -38,9 +38,13 @@ def _resolve(p):
     return out, th
 
 
-def table1(steps: int = 60000, nx: int = 100) -> dict:
+def table1(steps: int = 60000, nx: int = 100, fe_steps: int = 30000) -> dict:
     """Vapour-density errors (percent, signed: (rho_v - rho_v^Maxwell) / rho_v^Maxwell) keyed
-    ("FE", 1.0, tau_nu) and ("P", tau_q, tau_nu)."""
+    ("FE", 1.0, tau_nu) and ("P", tau_q, tau_nu).  The free-energy rows are read after
+    ``fe_steps``: at this condition (the model's stability limit, Sec. 5.1) the planar state
+    carries a period-2 density mode of a few percent of rho_v, and somewhere after 3.5e4 steps
+    (at a time that depends on rounding) a nonlinear event flips the sign of the vapour
+    density's deviation; before it, runs that differ by rounding agree to 1e-6."""
     import torch
 
     a, Tr, kappa = TABLE1_COND["a"], TABLE1_COND["Tr"], TABLE1_COND["kappa"]
@@ -68,7 +72,7 @@ def table1(steps: int = 60000, nx: int = 100) -> dict:
         ctx = L.Context(p, nx, 1)
         _, th = ctx.derived()
         ctx.set_density(inputs.flat_slab(nx, 1, th.rho_v, th.rho_l))
-        ctx.step(steps)
+        ctx.step(fe_steps)
         o = ctx.observables(L.FLAT)
         out[("FE", 1.0, tn)] = 100.0 * (o["rho_v"] - th.rho_v) / th.rho_v
         ctx.close()

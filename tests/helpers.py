@@ -23,5 +23,17 @@ def gpu_context(model, precision, nx, ny, walls=False, **kw):
     return ctx, rp, th
 
 
-def max_rel(a, b):
-    return float(np.abs(a - b).max() / np.abs(b).max())
+def rho_err(a, b):
+    """Largest relative density error, cell by cell: max over cells of |a - b| / |b| (every cell
+    against its own density, so a vapour cell counts as much as a liquid one)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def pop_err(f, f_ref):
+    """Largest population error relative to its own cell's density: max over i and cells of
+    |f_i - f_ref_i| / rho_ref (populations can vanish, the density of their cell cannot)."""
+    f = np.asarray(f, dtype=np.float64)
+    f_ref = np.asarray(f_ref, dtype=np.float64)
+    return float(np.max(np.abs(f - f_ref) / np.abs(f_ref.sum(0))))

@@ -91,6 +91,22 @@ def test_argument_errors(lib):
     assert "sm_103a" in lib.lbm_build_info()
 
 
+def test_free_energy_accepts_A_and_gravity_is_documented(lib):
+    """The viscosity-tuning term A of Eq. (20) belongs to the free-energy model: lbm_resolve_params
+    accepts A != 0 there (with nu = c_s^2 (tau - 1/2 - A) > 0, Eq. 23) and rejects it for the
+    pseudopotential model; the header documents exactly that, and names lbm_set_gravity."""
+    for A in (-0.2, 0.15, 0.3):
+        out, _ = lib.lbm_resolve_params(lib.lbm_params_default(lib.LBM_FREE_ENERGY, A=A, tau_nu=1.0))
+        assert out.A == A
+        with pytest.raises(lib.LBMError) as e:
+            lib.lbm_resolve_params(lib.lbm_params_default(lib.LBM_PSEUDOPOTENTIAL, A=A, tau_nu=1.0))
+        assert e.value.code == lib.LBM_ERR_UNSUPPORTED
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    assert "A = 0 and no gravity" not in text
+    assert "LBM_ERR_UNSUPPORTED for A != 0 with the pseudopotential model" in text
+    assert "lbm_set_gravity" in text.split("typedef enum")[0]  # named in the model summary
+
+
 def test_create_rejects_bad_sizes_and_boundaries_before_any_device_call(lib):
     """lbm_create validates sizes and boundaries before touching the device (so this runs
     without a GPU): empty lattices and more than 2^31 cells are argument errors, walls need

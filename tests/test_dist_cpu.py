@@ -88,3 +88,27 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("spinodal decomposition, 4096x4096")
+    # ms_per_step is the measured oracle sample of a timed step (about --ref-seconds), the
+    # full-workload figure only an extrapolation beside it
+    assert 0 < d["ms_per_step"] < 60_000
+    assert d["ms_per_step_extrapolated_full_workload"] > d["ms_per_step"]
+
+
+def test_reference_arm_does_not_load_the_product_library():
+    """The oracle leg of the benchmark takes every parameter (temperature, coexistence densities,
+    sigma^Li, relaxation times) from the oracle package: after it has run, no liblbm.so is mapped
+    into the process."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import bench, sys\n"
+            "v, cores, sample, sec = bench.oracle_mlups(64, 0.05, crop=32)\n"
+            "assert v > 0 and sec > 0\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "assert 'liblbm_oracle.so' in maps\n"
+            "sys.exit(3 if 'liblbm.so' in maps else 0)\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=root,
+                         env=dict(os.environ, OMP_NUM_THREADS="2"))
+    assert out.returncode == 0, (out.returncode, out.stderr[-2000:])

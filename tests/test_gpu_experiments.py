@@ -21,7 +21,7 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def _oracle_table1(steps, nx=100):
+def _oracle_table1(steps, fe_steps, nx=100):
     a, Tr, kappa = 0.5, 0.65, 0.5
     T = thermo.temperature(a, 4.0, 1.0, Tr)
     rv, rl, _ = thermo.maxwell(a, 4.0, 1.0, Tr)
@@ -36,31 +36,32 @@ def _oracle_table1(steps, nx=100):
             out[("P", tq, tn)] = 100 * (0.5 * (r[0] + r[-1]) - rv) / rv
     for tn in (0.55, 0.75, 1.0, 1.2):
         p = O.make_params(a=a, b=4.0, R=1.0, T=T, kappa=kappa, tau_nu=tn, tau_e=1.0, tau_zeta=1.0, tau_q=1.0)
-        r = O.macro(O.FE, p, O.run(O.FE, p, O.init(O.FE, rho0), steps))[0][0]
+        r = O.macro(O.FE, p, O.run(O.FE, p, O.init(O.FE, rho0), fe_steps))[0][0]
         out[("FE", 1.0, tn)] = 100 * (0.5 * (r[0] + r[-1]) - rv) / rv
     return out
 
 
 def test_table1_batched_against_oracle(paper_numbers):
-    """Table 1 on the GPU (P rows one FP32 batch, FE rows FP64 contexts, 6e4 steps) against
-    the oracle and the paper's pattern.  P vapour densities agree with the oracle within the
-    FP32 static bar, 5e-5 (measured <= 5e-6).  FE (FP64) within 3e-4: Tr = 0.65 at a = 0.5 is
-    the free-energy model's stability limit (Sec. 5.1); from a tanh start its planar state is
-    still wandering after 6e4 steps (the oracle's own values move between 0.089% and 0.114%
-    with tau_nu), and rounding-level differences between two FP64 programs reach 1.4e-4.
+    """Table 1 on the GPU (P rows one FP32 batch for 6e4 steps, FE rows FP64 contexts for 3e4
+    steps) against the oracle and the paper's pattern.  P vapour densities agree with the
+    oracle within the FP32 static bar, 1e-5.  FE (FP64) within 1e-5 as well: Tr = 0.65 at
+    a = 0.5 is the free-energy model's stability limit (Sec. 5.1); its planar state carries a
+    period-2 density mode of 3-4% of rho_v, and after about 3.5e4 steps a nonlinear event whose
+    timing depends on rounding flips the sign of the vapour deviation (the oracle's own values
+    at 6e4 steps spread by 2e-4 under 1e-15 perturbations of the start), so the rows are read
+    at 3e4 steps, where 1e-15 perturbations move them by less than 1e-6.
     Pattern: FE of the order of the printed 0.0605% for every tau_nu; P with tau_q = 1/1.99
     flat in tau_nu; P with tau_q = 1 falling with tau_nu; both P rows equal at tau_nu = 1."""
     from paper_2403_11167_gb300 import experiments
 
-    steps = 60000
-    gpu = experiments.table1(steps=steps)
-    ref = _oracle_table1(steps)
+    steps, fe_steps = 60000, 30000
+    gpu = experiments.table1(steps=steps, fe_steps=fe_steps)
+    ref = _oracle_table1(steps, fe_steps)
     for k in sorted(ref):
         print(f"Table 1 {k}: GPU {gpu[k]:+.5f}%  oracle {ref[k]:+.5f}%  rho_v ratio - 1 = "
               f"{(1 + gpu[k] / 100) / (1 + ref[k] / 100) - 1:+.2e}")
     for k in sorted(ref):
-        tol = 5e-5 if k[0] == "P" else 3e-4  # see the docstring
-        assert abs((1 + gpu[k] / 100) / (1 + ref[k] / 100) - 1) < tol, k
+        assert abs((1 + gpu[k] / 100) / (1 + ref[k] / 100) - 1) < 1e-5, k
     fe = [abs(gpu[("FE", 1.0, t)]) for t in (0.55, 0.75, 1.0, 1.2)]
     # same order as the printed 0.0605% for every tau_nu (the discrete planar relation gives 0.054%)
     assert max(fe) < 3 * paper_numbers["table1_fe_vapour_error_percent"]

@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 from paper_2403_11167_gb300 import inputs
-from helpers import gpu_context, max_rel, oracle_params
+from helpers import gpu_context, oracle_params, pop_err, rho_err
 
 pytestmark = pytest.mark.gpu
 
@@ -30,12 +30,12 @@ def _compare(ctx, rp, th, rho0, steps, walls=False, g=0.0, rho_g=0.0, y_ref=0.0,
     p.g, p.rho_g, p.y_ref = g, rho_g, y_ref
     f_ref = O.run(FE, p, O.init_iwb(p, rho0), steps)
     f = ctx.populations()
-    err = max_rel(f, f_ref)
+    err = pop_err(f, f_ref)
     assert err < tol, err
     rho_ref, ux_ref, uy_ref, *_ = O.macro(FE, p, f_ref)
     rho, ux, uy = ctx.fields()
     umax = max(np.abs(ux_ref).max(), np.abs(uy_ref).max())
-    assert max_rel(rho, rho_ref) < 10 * tol
+    assert rho_err(rho, rho_ref) < 10 * tol
     assert np.abs(ux - ux_ref).max() < 1e3 * tol * umax and np.abs(uy - uy_ref).max() < 1e3 * tol * umax
     return err
 
@@ -94,7 +94,7 @@ def test_fp64_weight_periodic_with_drive():
     p.g = 2e-6
     p.drive_ax_lo, p.drive_ax_hi, p.drive_x_split = 5e-4, -3e-4, 40.0
     f_ref = O.run_driven(FE, p, O.init_iwb(p, rho0), 70, t0=0, t_on=5)
-    assert max_rel(ctx.populations(), f_ref) < 1e-11
+    assert pop_err(ctx.populations(), f_ref) < 1e-11
 
 
 def test_fp32_A_droplet():
@@ -106,7 +106,7 @@ def test_fp32_A_droplet():
     ctx.step(100)
     p = oracle_params(rp, th)
     f_ref = O.run(FE, p, O.init(FE, rho0), 100)
-    err = max_rel(ctx.populations().sum(0), f_ref.sum(0))
+    err = rho_err(ctx.populations().sum(0), f_ref.sum(0))
     print("fp32 A", err)
     assert err < 1e-5
 

@@ -1,11 +1,14 @@
 """GPU parity: the sm_103a kernels (through the C ABI) against the FP64 oracle.
 
-Tolerances: FP64 runs agree to rounding (relative 1e-11 on populations after tens
-of steps) and meet the stated static bar (max relative density error 1e-5 after 1e4
-steps) by orders of magnitude.  FP32 runs meet the chaotic-run bar pointwise (1e-4 over
-the first 200 steps of a spinodal run, also at 4096^2); on static interfaces their
-observables meet 1e-5 while pointwise densities are held to the FP32 envelope of the
-methods' neutral modes, 5e-5 (see test_static_droplet_1e4_steps).
+Metric: densities cell by cell, max |rho_gpu - rho_oracle| / rho_oracle (helpers.rho_err);
+populations relative to their own cell's density (helpers.pop_err).  Tolerances: FP64 runs
+agree to rounding (1e-11 on populations after tens of steps) and meet the stated static bar
+(1e-5 after 1e4 steps) by orders of magnitude.  FP32 runs meet both stated bars as written:
+1e-5 on static droplets and slabs after 1e4 steps, and 1e-4 over the first 200 steps of a
+spinodal run (also at the benchmark's 4096^2 size).  What makes FP32 reach the static bar is
+the arithmetic of lbm_kernels.cuh: mirror-equivariant sums (no rigid drift of a symmetric
+state), scale-exact c_s^2 and stencil weights (no spurious EOS term in the pseudopotential
+model) and the compensated rest population of the free-energy model (no mass random walk).
 """
 import os
 import tempfile
@@ -16,7 +19,7 @@ import pytest
 import oracle as O
 from oracle import observables as OO
 from paper_2403_11167_gb300 import inputs
-from helpers import gpu_context, max_rel, oracle_params
+from helpers import gpu_context, oracle_params, pop_err, rho_err
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +53,7 @@ def test_fp64_random_fields(model, shape):
     ctx.set_density(rho0)
     ctx.step(25)
     f_ref = _oracle_run(model, rp, th, rho0, 25)
-    assert max_rel(ctx.populations(), f_ref) < 1e-11
+    assert pop_err(ctx.populations(), f_ref) < 1e-11
 
 
 @pytest.mark.parametrize("model", [PP, FE])
@@ -62,7 +65,7 @@ def test_fp32_random_fields(model):
     ctx.step(20)
     f_ref = _oracle_run(model, rp, th, rho0, 20)
     rho_gpu = ctx.populations().sum(0)
-    assert max_rel(rho_gpu, f_ref.sum(0)) < 1e-5
+    assert rho_err(rho_gpu, f_ref.sum(0)) < 1e-5
 
 
 def test_flat_interface_fp64_config():
@@ -77,7 +80,7 @@ def test_flat_interface_fp64_config():
     f_ref = _oracle_run(PP, rp, th, rho0, steps)
     rho_ref, ux_ref, uy_ref, *_ = O.macro(PP, oracle_params(rp, th), f_ref)
     rho_gpu, ux_gpu, uy_gpu = ctx.fields()
-    assert max_rel(rho_gpu, rho_ref) < 1e-11
+    assert rho_err(rho_gpu, rho_ref) < 1e-11
     ref = OO.observables(rho_ref, ux_ref, uy_ref, 0, rp.a, rp.b, rp.R, th.T)
     for k in ("rho_l", "rho_v", "width", "dp", "mass"):
         assert abs(obs[k] / ref[k] - 1) < 1e-9, k
@@ -89,15 +92,10 @@ def test_flat_interface_fp64_config():
 @pytest.mark.parametrize("model", [PP, FE])
 def test_static_droplet_1e4_steps(model, precision):
     """Static droplet (ragged 130 x 126 lattice, R = 25, Tr 0.8, a = 0.25, P parameters matched
-    to FE kappa = 0.5), 1e4 steps.
-
-    FP64 meets the stated bar (max relative density error <= 1e-5) by orders of magnitude.
-    FP32 populations do not, pointwise: both models have neutral modes that FP32 rounding
-    random-walks -- rigid translation of the droplet (P; momentum rounding, measured centre-of-
-    mass drift ~4e-5 cells) and the period-2 density mode of the well-balanced scheme (FE;
-    measured in the liquid core) -- so the pointwise bound checked here is the measured drift
-    envelope, 5e-5, while the observables (probe means, equimolar radius), which average
-    over the neutral modes, are held to 1e-5."""
+    to FE kappa = 0.5), 1e4 steps: density cell by cell within 1e-5 of the oracle (the stated
+    static bar; FP64 meets it by orders of magnitude), the pair-averaged probe densities and
+    the equimolar radius within 1e-5, and the pressure jump of the Laplace test relative to
+    itself."""
     nx, ny, steps = 130, 126, 10000
     kw = dict(a=0.25, Tr=0.8, tau_nu=1.0)
     if model == PP:
@@ -109,18 +107,17 @@ def test_static_droplet_1e4_steps(model, precision):
     rho_gpu, ux_gpu, uy_gpu = ctx.fields()
     f_ref = _oracle_run(model, rp, th, rho0, steps)
     rho_ref, ux_ref, uy_ref, *_ = O.macro(model, oracle_params(rp, th), f_ref)
-    err = max_rel(rho_gpu, rho_ref)
-    assert err < (1e-9 if precision == F64 else 5e-5), err
+    err = rho_err(rho_gpu, rho_ref)
+    assert err < (1e-9 if precision == F64 else 1e-5), err
     obs = ctx.observables(1)
     ref = OO.observables(rho_ref, ux_ref, uy_ref, 1, rp.a, rp.b, rp.R, th.T)
     for k in ("rho_l", "rho_v", "radius"):
-        assert abs(obs[k] / ref[k] - 1) < 1e-5, k
-    # dp = p(rho_l) - p(rho_v): the 1e-5 density bar propagated through the EOS slope
-    from oracle import thermo
-
-    eos = thermo.EOS(rp.a, rp.b, rp.R)
-    dp_tol = 1e-5 * (abs(eos.dp(ref["rho_l"], th.T)) * ref["rho_l"] + abs(eos.dp(ref["rho_v"], th.T)) * ref["rho_v"])
-    assert abs(obs["dp"] - ref["dp"]) < dp_tol
+        assert abs(obs[k] / ref[k] - 1) < (1e-9 if precision == F64 else 1e-5), k
+    # dp = p(rho_l) - p(rho_v) (Sec. 5.2) relative to itself: 1e-9 in FP64; in FP32 the probe
+    # densities carry the FP32 rounding of the stored state (~6e-8) and the EOS slope
+    # p'(rho_l) rho_l / dp ~ 200 at R = 25 amplifies it, so the bar is 1e-3 of dp -- the
+    # accuracy to which the Laplace slope is read
+    assert abs(obs["dp"] / ref["dp"] - 1) < (1e-9 if precision == F64 else 1e-3), (obs["dp"], ref["dp"])
 
 
 @pytest.mark.parametrize("model", [PP, FE])
@@ -137,7 +134,7 @@ def test_spinodal_fp32_first_200_steps(model):
     for chunk in range(4):
         ctx.step(50)
         f = O.run(model, op, f, 50)
-        worst = max(worst, max_rel(ctx.fields()[0], O.macro(model, op, f)[0]))
+        worst = max(worst, rho_err(ctx.fields()[0], O.macro(model, op, f)[0]))
     assert worst < 1e-4
 
 
@@ -162,7 +159,8 @@ def test_full_size_4096_sampled(model):
         crop = rho0[np.ix_(ys, xs)]
         fc = O.run(model, op, O.init(model, crop), steps)
         ref = fc[:, h, h]
-        assert np.abs(got[k] - ref).max() / np.abs(ref).max() < 1e-5, (x, y)
+        assert abs(got[k].sum() / ref.sum() - 1) < 1e-5, (x, y)
+        assert np.abs(got[k] - ref).max() / ref.sum() < 1e-5, (x, y)
     ctx.close()
 
 
@@ -171,7 +169,7 @@ def test_full_size_4096_sampled_200_steps(model):
     """The chaotic-run bar at the benchmark's size: the 4096^2 spinodal lattice in the
     benchmark's launch configuration, 200 FP32 steps, populations at 3 sampled cells against
     the oracle on each cell's periodic domain-of-dependence crop (805^2 for P, 1205^2 for FE);
-    max relative error <= 1e-4."""
+    relative density error of each sampled cell <= 1e-4 (and each population relative to it)."""
     nx = ny = 4096
     steps = 200
     ctx, rp, th = gpu_context(model, F32, nx, ny, a=0.25, Tr=0.85, tau_nu=0.8)
@@ -187,7 +185,8 @@ def test_full_size_4096_sampled_200_steps(model):
         xs = np.arange(x - h, x + h + 1) % nx
         fc = O.run(model, op, O.init(model, rho0[np.ix_(ys, xs)]), steps)
         ref = fc[:, h, h]
-        assert np.abs(got[k] - ref).max() / np.abs(ref).max() < 1e-4, (x, y)
+        assert abs(got[k].sum() / ref.sum() - 1) < 1e-4, (x, y)  # the cell's density
+        assert np.abs(got[k] - ref).max() / ref.sum() < 1e-4, (x, y)  # each population
     ctx.close()
 
 
@@ -218,10 +217,13 @@ def test_graph_replay_equals_single_launches(model):
     assert np.array_equal(a.populations(), b.populations())
 
 
-def test_checkpoint_roundtrip():
-    """n + m steps equal n steps, save, load into a fresh context, m steps (bitwise)."""
-    nx, ny = 70, 50
-    a, rp, th = gpu_context(PP, F32, nx, ny, Tr=0.8)
+@pytest.mark.parametrize("model,nx", [(PP, 70), (FE, 70), (FE, 72)])
+def test_checkpoint_roundtrip(model, nx):
+    """n + m steps equal n steps, save, load into a fresh context, m steps (bitwise; for the
+    FP32 free-energy model this includes the rest population's extension, on the direct kernel
+    (nx = 70) and on the strip kernel (nx = 72))."""
+    ny = 50
+    a, rp, th = gpu_context(model, F32, nx, ny, Tr=0.8)
     rho0 = inputs.droplet(nx, ny, 15.0, th.rho_v, th.rho_l)
     a.set_density(rho0)
     a.step(150)
@@ -229,11 +231,38 @@ def test_checkpoint_roundtrip():
         path = os.path.join(d, "ck.bin")
         a.save(path)
         a.step(77)
-        b, _, _ = gpu_context(PP, F32, nx, ny, Tr=0.8)
+        b, _, _ = gpu_context(model, F32, nx, ny, Tr=0.8)
         b.load(path)
         assert b.observables(1)["step"] == 150
         b.step(77)
     assert np.array_equal(a.populations(), b.populations())
+
+
+def test_checkpoint_rejects_other_parameters():
+    """A checkpoint continues the run it came from: loading it into a context of another
+    temperature (or any other resolved parameter) is an argument error, and the context keeps
+    its own state."""
+    from paper_2403_11167_gb300 import lbm
+
+    nx, ny = 40, 24
+    a, rp, th = gpu_context(FE, F32, nx, ny, Tr=0.8)
+    a.set_density(inputs.droplet(nx, ny, 8.0, th.rho_v, th.rho_l))
+    a.step(10)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        a.save(path)
+        for kw in (dict(Tr=0.75), dict(Tr=0.8, kappa=0.6), dict(Tr=0.8, tau_nu=0.9)):
+            b, _, th_b = gpu_context(FE, F32, nx, ny, **kw)
+            b.set_density(inputs.droplet(nx, ny, 8.0, th_b.rho_v, th_b.rho_l))
+            before = b.populations()
+            with pytest.raises(lbm.LBMError) as e:
+                b.load(path)
+            assert e.value.code == lbm.LBM_ERR_ARG, kw
+            assert np.array_equal(b.populations(), before)
+            b.close()
+        c, _, _ = gpu_context(FE, F32, nx, ny, Tr=0.8)
+        c.load(path)
+        assert np.array_equal(c.populations(), a.populations())
 
 
 def test_set_get_populations_roundtrip():
@@ -282,4 +311,4 @@ def test_tma_pipeline_matches_direct_kernel(model, shape, monkeypatch):
     fa, fb = a.populations(), b.populations()
     assert np.abs(fa - fb).max() <= 1e-7 * np.abs(fb).max()
     f_ref = _oracle_run(model, rp, th, rho0, 50)
-    assert max_rel(fa.sum(0), f_ref.sum(0)) < 1e-5
+    assert rho_err(fa.sum(0), f_ref.sum(0)) < 1e-5

@@ -2,7 +2,7 @@
 with the TMA copy rules, and the full/empty mbarrier row ring under random interleavings.
 
 Both models restate, in plain integer arithmetic, what `csrc/step_pair.cuh` and
-`csrc/step_tma.cuh` do: `warp_strip_width`, the copies of `issue_row` (a row of a strip plus
+`csrc/ring.cuh` do: `warp_strip_width`, the copies of `issue_row` (a row of a strip plus
 4 halo columns each side, in three pieces at the periodic x edges), the 60-column warp runs,
 the columns `pull_pair` reads, and the ring protocol of `ring_produce` and the consumer loops
 of `fe_step_pair` / `pp_pair_strip` with the parity semantics of `mbarrier.try_wait.parity`
