@@ -279,7 +279,7 @@ typedef struct lbm_batch lbm_batch;
 
 /* Create a batch of n lattices.  rho0[i]: host array of nx*ny densities of lattice i
  * (copied; f starts at f^eq(rho0, u = 0)).  Lattices whose populations, psi and rho fit in
- * one CTA's shared memory (11 nx ny floats <= 200 KB, up to 4654 cells) run resident: one CTA
+ * one CTA's shared memory (11 nx ny floats and nx ny int16 <= 200 KB, up to 4452 cells) run resident: one CTA
  * each, all steps in shared memory, in one persistent launch.  The others run as strips
  * of a work table, one launch per step for all of them, replayed as 64-step CUDA graphs on
  * a second stream concurrently.  An autotuner picks the resident block size and the strip

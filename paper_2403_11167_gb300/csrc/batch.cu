@@ -6,7 +6,8 @@
 // lattices of uneven sizes and step counts.  Run one at a time, the small ones are
 // launch-latency bound and the large ones leave most SMs idle.  Here they run together:
 //
-//   resident lattices  -- populations (9 N floats) + psi (N floats) fit in one CTA's shared
+//   resident lattices  -- populations (9 N floats, the rest extensions N int16) + psi and
+//                         rho (2 N floats) fit in one CTA's shared
 //                         memory: one CTA per lattice runs every step of that lattice in
 //                         shared memory, in one persistent launch (no HBM traffic per step);
 //   tiled lattices     -- the rest: a work table of (lattice, strip) items; one launch per
@@ -35,6 +36,7 @@
 #include "lbm_kernels.cuh"
 #include "ring.cuh"
 #include "step_pair.cuh"
+#include "rest_host.h"
 
 namespace {
 
@@ -74,6 +76,13 @@ struct BatchItem {
 
 size_t a256(size_t n) { return (n + 255) & ~size_t(255); }
 
+// Shared memory of a resident lattice of N cells: 9 population planes, psi and rho (FP32), and
+// the int16 extensions of the rest population.
+size_t resident_bytes(size_t N) { return 11 * N * sizeof(float) + ((2 * N + 15) & ~size_t(15)); }
+
+// One population buffer of a lattice: 9 FP32 planes plus the int16 rest plane (plane 9).
+size_t buffer_bytes(long long pitch) { return a256(10 * (size_t)pitch * 4); }
+
 }  // namespace
 
 namespace lbmk {
@@ -95,12 +104,14 @@ __global__ void __launch_bounds__(1024, 1)
     float* S = rsm;            // 9 planes of N
     float* psi = rsm + 9 * N;  // N
     float* rho = psi + N;      // N
+    short* Q = reinterpret_cast<short*>(rho + N);  // N: rest-population extensions
     const float* g0 = L.buf[0];
     float* G = L.buf[1];
     for (int idx = threadIdx.x; idx < 9 * N; idx += blockDim.x) {
         const int i = idx / N, c = idx - i * N;
         S[idx] = g0[i * pitch + c];
     }
+    for (int c = threadIdx.x; c < N; c += blockDim.x) Q[c] = rest_lo_plane(g0, pitch)[c];
     __syncthreads();
     const int nsteps = step_limit >= 0 ? min(step_limit, L.nsteps) : L.nsteps;
     for (int s = 0; s < nsteps; ++s) {
@@ -117,7 +128,9 @@ __global__ void __launch_bounds__(1024, 1)
             float v[9], pn[9];
             pull_cell_shared(S, N, x, y, nx, ny, v);
             gather8(psi, x, y, nx, ny, pn);
-            pp_collide(v, rho[c], pn[0], pn, P);
+            int q = Q[c];  // compensated rest population (only this thread touches Q[c])
+            pp_collide_comp(v, q, rho[c], pn[0], pn, P);
+            Q[c] = (short)q;
 #pragma unroll
             for (int i = 0; i < 9; ++i) G[i * pitch + c] = v[i];
         }
@@ -134,6 +147,7 @@ __global__ void __launch_bounds__(1024, 1)
         const int i = idx / N, c = idx - i * N;
         g[i * pitch + c] = S[idx];
     }
+    for (int c = threadIdx.x; c < N; c += blockDim.x) rest_lo_plane(g, pitch)[c] = Q[c];
 }
 
 // Tiled lattices, two cells per lane: one strip of one lattice per CTA, one step per launch.
@@ -167,7 +181,7 @@ __global__ void batch_obs_kernel(const BatchLattice* __restrict__ lats, double* 
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         float v[9];
         pull_cell(f, P.pitch, c % nx, c / nx, nx, ny, v);
-        const float r = sum9(v);
+        const float r = sum9_rest(v, rest_lo_plane(f, P.pitch)[c], P);
         rho[c] = r;
         ps[c] = pseudo_psi(r, P);
     }
@@ -298,7 +312,8 @@ int batch_init_state(lbm_batch* b) {
         const size_t n = (size_t)L.P.nx * L.P.ny;
         BCK(cudaMemcpyAsync(L.scratch, b->rho0[i].data(), n * sizeof(double), cudaMemcpyHostToDevice, b->s_tile));
         lbmk::init_kernel<float, double><<<std::min<long long>(304, (n + 255) / 256), 256, 0, b->s_tile>>>(
-            reinterpret_cast<const double*>(L.scratch), L.buf[0], LBM_PSEUDOPOTENTIAL, L.P.nx, L.P.ny, L.P.pitch);
+            reinterpret_cast<const double*>(L.scratch), L.buf[0], LBM_PSEUDOPOTENTIAL, L.P.nx, L.P.ny, L.P.pitch,
+            L.P.rest_inv);
     }
     BCK(cudaGetLastError());
     const int zero = 0;
@@ -538,20 +553,21 @@ extern "C" int lbm_batch_create(int n, const lbm_batch_lattice* specs, const dou
         P.s_nu = (float)(1.0 / rp.tau_nu);
         P.fx = (float)rp.body_fx;
         P.fy = (float)rp.body_fy;
+        P.rest_unit = (float)lbm_host::rest_unit(rp.b);
+        P.rest_inv = (float)lbm_host::rest_inv(rp.b);
         L.RT = rp.R * th.T;
         L.a = rp.a;
         L.b4 = 0.25 * rp.b;
         L.nsteps = (int)s.nsteps;
         L.geometry = s.geometry;
-        const size_t smem = 11 * N * sizeof(float);
-        L.resident = smem <= kResidentSmemMax;
+        L.resident = resident_bytes(N) <= kResidentSmemMax;
         if (!L.resident && (s.nx % 4 != 0 || s.nx < 8 || s.ny < 4)) {
             delete b;
             return LBM_ERR_UNSUPPORTED;  // tiled lattices use the TMA strip kernels
         }
         if (!L.resident) b->max_tiled_steps = std::max(b->max_tiled_steps, L.nsteps);
         offs[i] = pool_bytes;
-        pool_bytes += 2 * a256(9 * (size_t)P.pitch * 4) + a256(2 * N * 4 + 8 * N);
+        pool_bytes += 2 * buffer_bytes(P.pitch) + a256(2 * N * 4 + 8 * N);
     }
     const size_t tail = pool_bytes;
     pool_bytes += a256(sizeof(BatchLattice) * n) + a256(sizeof(int) * n) + 256 + 256 + a256(8 * sizeof(double) * n);
@@ -563,13 +579,13 @@ extern "C" int lbm_batch_create(int n, const lbm_batch_lattice* specs, const dou
     size_t smax = 0;
     for (int i = 0; i < n; ++i) {
         BatchLattice& L = b->lat[i];
-        const size_t fb = a256(9 * (size_t)L.P.pitch * 4);
+        const size_t fb = buffer_bytes(L.P.pitch);
         L.buf[0] = reinterpret_cast<float*>(b->pool + offs[i]);
         L.buf[1] = reinterpret_cast<float*>(b->pool + offs[i] + fb);
         L.scratch = reinterpret_cast<float*>(b->pool + offs[i] + 2 * fb);
         if (L.resident) {
             b->resident_ids.push_back(i);
-            smax = std::max(smax, (size_t)L.P.nx * L.P.ny * 11 * sizeof(float));
+            smax = std::max(smax, resident_bytes((size_t)L.P.nx * L.P.ny));
         }
     }
     std::stable_sort(b->resident_ids.begin(), b->resident_ids.end(), [&](int x, int y) {
@@ -690,6 +706,10 @@ extern "C" int lbm_batch_populations(lbm_batch* b, int i, double* f) {
                 f[q * n + (size_t)ys * nx + xs] = plane[(size_t)y * nx + x];
             }
     }
+    std::vector<short> ext(n);  // the rest population's extension (plane 9)
+    BCK(cudaMemcpy(ext.data(), reinterpret_cast<const char*>(src + 9 * L.P.pitch), n * sizeof(short),
+                   cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < n; ++k) f[k] = lbm_host::rest_decode((float)f[k], ext[k], (double)L.P.rest_unit);
     return LBM_OK;
 }
 

@@ -18,6 +18,7 @@
 #include "ring.cuh"
 #include "step_pair.cuh"
 #include "step_ext.cuh"
+#include "rest_host.h"
 #include "thermo.h"
 
 namespace {
@@ -344,6 +345,8 @@ static void fill_step_params(lbmk::StepParams<real>& s, const lbm_ctx* c) {
     s.s_nu = (real)(1.0 / p.tau_nu);
     s.fx = (real)p.body_fx;
     s.fy = (real)p.body_fy;
+    s.rest_unit = (real)lbm_host::rest_unit(p.b);
+    s.rest_inv = (real)lbm_host::rest_inv(p.b);
 }
 
 static int choose_rows(int nx, int ny, int tx, int strips_per_sm) {
@@ -768,10 +771,10 @@ static int launch_init(lbm_ctx* c, const src_t* rho0_dev) {
         const double coef = c->rho_g * c->g;
         if (c->prec == LBM_F32)
             lbmk::init_iwb_kernel<float, src_t><<<kRedBlocks, 256, 0, c->stream>>>(
-                rho0_dev, (float*)c->f[0], c->nx, c->ny, c->pitch, coef, c->y_ref);
+                rho0_dev, (float*)c->f[0], c->nx, c->ny, c->pitch, coef, c->y_ref, c->spf.rest_inv);
         else
             lbmk::init_iwb_kernel<double, src_t><<<kRedBlocks, 256, 0, c->stream>>>(
-                rho0_dev, (double*)c->f[0], c->nx, c->ny, c->pitch, coef, c->y_ref);
+                rho0_dev, (double*)c->f[0], c->nx, c->ny, c->pitch, coef, c->y_ref, 0.0f);
         CK(cudaGetLastError());
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
         c->cur = 0;
@@ -782,10 +785,11 @@ static int launch_init(lbm_ctx* c, const src_t* rho0_dev) {
     }
     if (c->prec == LBM_F32)
         lbmk::init_kernel<float, src_t>
-            <<<kRedBlocks, 256, 0, c->stream>>>(rho0_dev, (float*)c->f[0], model, c->nx, c->ny, c->pitch);
+            <<<kRedBlocks, 256, 0, c->stream>>>(rho0_dev, (float*)c->f[0], model, c->nx, c->ny, c->pitch,
+                                                c->spf.rest_inv);
     else
         lbmk::init_kernel<double, src_t>
-            <<<kRedBlocks, 256, 0, c->stream>>>(rho0_dev, (double*)c->f[0], model, c->nx, c->ny, c->pitch);
+            <<<kRedBlocks, 256, 0, c->stream>>>(rho0_dev, (double*)c->f[0], model, c->nx, c->ny, c->pitch, 0.0f);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     c->cur = 0;
@@ -820,24 +824,8 @@ static inline size_t shifted(int x, int y, int i, int nx, int ny) {
     return (size_t)ys * nx + xs;
 }
 
-// Host view of the compensated rest population of FP32 free-energy buffers (see
-// lbmk::rest_update): f_0 = hi + q 2^-16 ulp(hi).
-static bool has_rest_plane(const lbm_ctx* c) { return c->prec == LBM_F32 && c->prm.model == LBM_FREE_ENERGY; }
-static int float_exponent_bits(float hi) {
-    uint32_t b;
-    std::memcpy(&b, &hi, 4);
-    return (int)((b >> 23) & 0xff);
-}
-static double rest_decode(float hi, short q) {
-    const int e = float_exponent_bits(hi);
-    return (double)hi + (e > 39 ? std::ldexp((double)q, e - 166) : 0.0);
-}
-static short rest_encode_host(double v, float hi) {
-    const int e = float_exponent_bits(hi);
-    if (e <= 39) return 0;
-    const double q = std::nearbyint(std::ldexp(v - (double)hi, 166 - e));
-    return (short)std::max(-32767.0, std::min(32767.0, q));
-}
+// FP32 buffers carry the compensated rest population (lbmk::rest_update; rest_host.h).
+static bool has_rest_plane(const lbm_ctx* c) { return c->prec == LBM_F32; }
 
 extern "C" int lbm_set_populations(lbm_ctx* c, const double* f) {
     if (!c || !f) return LBM_ERR_ARG;
@@ -858,10 +846,9 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f) {
                       cudaMemcpyHostToDevice));
     }
     if (c->prec == LBM_F32) {
-        // rest-population extension: the part of f_0 below FP32 (free energy), else zero
+        // rest-population extension: the part of f_0 below FP32
         std::vector<short> q(n, 0);
-        if (has_rest_plane(c))
-            for (size_t k = 0; k < n; ++k) q[k] = rest_encode_host(f[k], (float)f[k]);
+        for (size_t k = 0; k < n; ++k) q[k] = lbm_host::rest_encode(f[k], (float)f[k], lbm_host::rest_inv(c->prm.b));
         CK(cudaMemcpy(static_cast<char*>(c->f[0]) + (size_t)9 * c->pitch * 4, q.data(), n * sizeof(short),
                       cudaMemcpyHostToDevice));
     }
@@ -905,7 +892,7 @@ extern "C" int lbm_get_populations(lbm_ctx* c, double* f) {
         std::vector<short> q(n);
         CK(cudaMemcpy(q.data(), static_cast<char*>(c->f[c->cur]) + (size_t)9 * c->pitch * 4, n * sizeof(short),
                       cudaMemcpyDeviceToHost));
-        for (size_t k = 0; k < n; ++k) f[k] = rest_decode((float)f[k], q[k]);
+        for (size_t k = 0; k < n; ++k) f[k] = lbm_host::rest_decode((float)f[k], q[k], lbm_host::rest_unit(c->prm.b));
     }
     return LBM_OK;
 }
@@ -930,7 +917,7 @@ extern "C" int lbm_get_populations_at(lbm_ctx* c, int n, const int* xs, const in
                     short q;
                     const size_t qoff = (size_t)9 * c->pitch * 4 + ((size_t)ys_ * c->nx + xs_) * sizeof(short);
                     CK(cudaMemcpy(&q, static_cast<char*>(c->f[c->cur]) + qoff, sizeof(short), cudaMemcpyDeviceToHost));
-                    out[9 * k] = rest_decode(v, q);
+                    out[9 * k] = lbm_host::rest_decode(v, q, lbm_host::rest_unit(c->prm.b));
                 }
             } else {
                 CK(cudaMemcpy(&out[9 * k + i], static_cast<char*>(c->f[c->cur]) + off, 8, cudaMemcpyDeviceToHost));

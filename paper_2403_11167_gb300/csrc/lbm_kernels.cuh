@@ -37,6 +37,7 @@ struct StepParams {
     real irr_v, irr_l; // 1 / rho_ref
     real s_e, s_z, s_q, s_nu;  // relaxation rates 1/tau (Eq. 3); tau_rho, tau_j drop out
     real fx, fy;       // body force
+    real rest_unit, rest_inv;  // FP32: unit of the rest population's extension and its inverse
 };
 
 // Correctly rounded reciprocal (FP32: one hardware-assisted sequence instead of a full division).
@@ -362,7 +363,12 @@ __device__ __forceinline__ F fe_mu_v(F rc, const F rn[9], const StepParams<float
 
 // f* = f + M^-1 dm (Eq. S49) in the FP32 arithmetic.  COMP: the rest population's increment
 // goes to *d0 and v[0] is left unchanged (compensated rest population, see rest_update).
-template <class F, bool COMP = false>
+// ABSORB (with COMP): each moving population's rounding error, inc - (fl(f + inc) - f) (exact
+// by Fast2Sum when |f| >= |inc|), is added to *d0 as well, so the rest population takes up
+// what the moving ones lost and the cell's mass changes only by rounding of the increments
+// (relative ~1e-7 of them) -- needed where the moving populations carry much of the mass
+// (pseudopotential model, f_i = w_i rho at rest).  The errors are summed in mirror pairs.
+template <class F, bool COMP = false, bool ABSORB = false>
 __device__ __forceinline__ void apply_dm_v(F v[9], F de, F dz, F djx, F dqx, F djy, F dqy, F dpxx, F dpxy,
                                            F* d0 = nullptr) {
     const F A = fmav(de, F::c(-1.0f / 36.0f), dz * F::c(-1.0f / 18.0f));
@@ -380,14 +386,28 @@ __device__ __forceinline__ void apply_dm_v(F v[9], F de, F dz, F djx, F dqx, F d
         *d0 = (dz - de) * F::c(1.0f / 9.0f);
     else
         v[0] = fmav(dz - de, F::c(1.0f / 9.0f), v[0]);
-    v[1] = v[1] + ((A + X1) + Pp);
-    v[2] = v[2] + ((A + Y1) - Pp);
-    v[3] = v[3] + ((A - X1) + Pp);
-    v[4] = v[4] + ((A - Y1) - Pp);
-    v[5] = v[5] + (((B + X2) + Y2) + Z);
-    v[6] = v[6] + (((B - X2) + Y2) - Z);
-    v[7] = v[7] + (((B - X2) - Y2) + Z);
-    v[8] = v[8] + (((B + X2) - Y2) - Z);
+    F inc[9];
+    inc[1] = (A + X1) + Pp;
+    inc[2] = (A + Y1) - Pp;
+    inc[3] = (A - X1) + Pp;
+    inc[4] = (A - Y1) - Pp;
+    inc[5] = ((B + X2) + Y2) + Z;
+    inc[6] = ((B - X2) + Y2) - Z;
+    inc[7] = ((B - X2) - Y2) + Z;
+    inc[8] = ((B + X2) - Y2) - Z;
+    if constexpr (COMP && ABSORB) {
+        F err[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const F n = v[i] + inc[i];
+            err[i] = inc[i] - (n - v[i]);
+            v[i] = n;
+        }
+        *d0 = *d0 + (((err[1] + err[3]) + (err[2] + err[4])) + ((err[5] + err[7]) + (err[6] + err[8])));
+    } else {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) v[i] = v[i] + inc[i];
+    }
 }
 
 // Improved well-balanced free-energy collision (Eqs. 1, 6, 20, 21, 24); mn, rn: mu and rho
@@ -451,8 +471,11 @@ __device__ __forceinline__ F pseudo_psi_v(F rho, const StepParams<float>& P) {
 
 // Modified pseudopotential collision (Eqs. 1, 4, 6, 10, 13, 30-32) in the algebra of pp_collide:
 // pc = psi at the cell, pn[i] = psi at x + c_i (i = 1..8).
-template <class F>
-__device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9], const StepParams<float>& P) {
+// COMP: compensated rest population with the moving populations' rounding absorbed (the rest
+// increment goes to *d0, v[0] unchanged; see apply_dm_v and rest_update).
+template <class F, bool COMP = false>
+__device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9], const StepParams<float>& P,
+                                             F* d0 = nullptr) {
     const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
     const F Sx = div12(stencil12_x(pn));
     const F Sy = div12(stencil12_y(pn));
@@ -495,45 +518,62 @@ __device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9],
                         F::c(-P.s_nu) * ((pxx - rho * fmav(ux, ux, -(uy * uy))) + (Qxx - Qyy)));
     const F dpxy = fmav(F::c(hn), fmav(ux, Fy, uy * Fx), F::c(-P.s_nu) * ((pxy - rho * ux * uy) + Qxy));
     // j* - j = F exactly (tau_j drops out)
-    apply_dm_v(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy);
+    apply_dm_v<F, COMP, COMP>(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy, d0);
 }
 
 // ---------------------------------------------------------------------------------
-// Compensated rest population of the FP32 free-energy model.
+// Compensated rest population of the FP32 step (both models).
 //
-// In the free-energy model the rest population carries almost all of a cell's mass (f_0 = rho
-// at rest, Eq. 20), so FP32 rounds the mass of every cell at ulp(rho) per step and the total
-// mass random-walks; the well-balanced scheme's neutral period-2 density mode and the droplet
-// radius follow (measured: 2e-5 .. 9e-5 relative density error after 1e4 static steps).  FP32
-// free-energy buffers therefore carry a tenth plane of int16 q per cell: the rest population
-// is hi + q 2^-16 ulp(hi), hi the FP32 value of plane 0 (about 40 significant bits).  Every
-// collision adds its rest increment d with an error-free transformation, so the stored mass
-// changes only by the rounding of the small moving populations.  The arithmetic of the step
-// reads hi only (rho = sum f_i in FP32); the observables and the host population views add q.
+// FP32 rounds every population of every cell at each step; in a static state the roundings
+// repeat step after step, so the cells' masses drift (linearly in the number of steps) and
+// the interfaces follow: measured 1e-5 .. 4e-4 relative density error after 1e4 static steps,
+// largest at low Tr where the liquid's rounding lands on a vapour ~700 times less dense.  In
+// the free-energy model the rest population carries almost all of a cell's mass (f_0 = rho at
+// rest, Eq. 20); in the pseudopotential model it carries 4/9 (f_i = w_i rho, Eq. 4).  FP32
+// buffers therefore carry a tenth plane of int16 q per cell: the rest population is hi + q u,
+// hi the FP32 value of plane 0 and u = 2^(e - 38) a per-lattice unit, e the binary exponent of
+// the Carnahan-Starling packing limit 4/b (every density is below it, so |hi| < 2^(e+1), the
+// rounding residual of hi is below 2^(e-24) = 2^14 u and q never leaves its 16 bits; for the
+// smallest vapour densities u is still 1e-8 of the value).  Every collision adds its rest
+// increment with an error-free transformation (rest_update); the pseudopotential collision
+// also hands the moving populations' rounding errors to it (apply_dm_v, ABSORB), so a cell's
+// stored mass changes only by the rounding of the small increments.  The arithmetic of the
+// step reads hi only (rho = sum f_i in FP32); the observables and the host population views
+// add q u.
 
-// 2^-16 ulp(hi) and its inverse (0 for |hi| < 2^-87, where q is ignored).
-__device__ __forceinline__ float rest_lo_unit(float hi) {
-    const int e = (__float_as_int(hi) >> 23) & 0xff;
-    return e > 39 ? __int_as_float((e - 39) << 23) : 0.0f;
-}
-__device__ __forceinline__ float rest_lo_inv_unit(float hi) {
-    const int e = (__float_as_int(hi) >> 23) & 0xff;
-    return e > 39 ? __int_as_float((293 - e) << 23) : 0.0f;
-}
-
-// (hi + q 2^-16 ulp(hi)) + d -> (hi, q), exact up to 2^-17 ulp of the new hi: TwoSum of hi and
-// d, the old q carried in the error term, Fast2Sum renormalisation.
-__device__ __forceinline__ void rest_update(float& hi, int& q, float d) {
-    const float lo = __fmul_rn((float)q, rest_lo_unit(hi));
-    const float s = __fadd_rn(hi, d);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));  // hi + d = s + err
-    const float t = __fadd_rn(err, lo);
-    const float h2 = __fadd_rn(s, t);
-    const float l2 = __fsub_rn(t, __fsub_rn(h2, s));  // s + t = h2 + l2
-    const int qn = __float2int_rn(__fmul_rn(l2, rest_lo_inv_unit(h2)));
-    q = max(-32767, min(32767, qn));
+// (hi + qf u) + d -> (hi, qf), qf the extension held as an (integer-valued) float: TwoSum of
+// hi and d, the old extension carried in the error term, Fast2Sum renormalisation, qf the
+// residual rounded to a multiple of u.  Written once for one cell (F1) or two (F2).
+template <class F>
+__device__ __forceinline__ void rest_update_v(F& hi, F& qf, F d, const StepParams<float>& P) {
+    const F lo = qf * F::c(P.rest_unit);
+    const F s = hi + d;
+    const F bb = s - hi;
+    const F err = (hi - (s - bb)) + (d - bb);  // hi + d = s + err exactly
+    const F t = err + lo;
+    const F h2 = s + t;
+    const F l2 = t - (h2 - s);  // s + t = h2 + l2
     hi = h2;
+    qf = l2 * F::c(P.rest_inv);
+}
+
+// Extension <-> int16 storage (rounded to nearest, clamped to +-32767).
+__device__ __forceinline__ float rest_q_float(int q) { return (float)q; }
+__device__ __forceinline__ int rest_q_int(float qf) { return max(-32767, min(32767, __float2int_rn(qf))); }
+
+// Single cell: hi and its int16 q updated by the rest increment d.
+__device__ __forceinline__ void rest_update(float& hi, int& q, float d, const StepParams<float>& P) {
+    F1 h(hi), qf(rest_q_float(q));
+    rest_update_v(h, qf, F1(d), P);
+    hi = h.v;
+    q = rest_q_int(qf.v);
+}
+
+// Two cells of a lane (packed FP32): w holds both int16 extensions (first cell low half).
+__device__ __forceinline__ unsigned rest_update_pair(F2& hi, unsigned w, F2 d, const StepParams<float>& P) {
+    F2 qf(rest_q_float((int)(short)(w & 0xffffu)), rest_q_float((int)w >> 16));
+    rest_update_v(hi, qf, d, P);
+    return ((unsigned)rest_q_int(qf.v.x) & 0xffffu) | ((unsigned)rest_q_int(qf.v.y) << 16);
 }
 
 // The rest-population plane of an FP32 buffer (plane 9, int16).
@@ -544,21 +584,16 @@ __device__ __forceinline__ const short* rest_lo_plane(const float* f, long long 
     return reinterpret_cast<const short*>(f + 9 * pitch);
 }
 
-// q of a value v given its FP32 rounding hi (0 when v carries no more than FP32).
-template <typename src_t>
-__device__ __forceinline__ short rest_encode(src_t v, float hi) {
-    if constexpr (std::is_same<src_t, double>::value) {
-        const double q = rint((v - (double)hi) * (double)rest_lo_inv_unit(hi));
-        return (short)fmax(-32767.0, fmin(32767.0, q));
-    } else {
-        return 0;
-    }
+// q of a value v (FP64) given its FP32 rounding hi and the inverse unit of the lattice.
+__device__ __forceinline__ short rest_encode(double v, float hi, float rest_inv) {
+    const double q = rint((v - (double)hi) * (double)rest_inv);
+    return (short)fmax(-32767.0, fmin(32767.0, q));
 }
 
-// rho of pulled FP32 free-energy populations including the rest population's extension q.
-__device__ __forceinline__ float sum9_rest(const float v[9], int q) {
+// rho of pulled FP32 populations including the rest population's extension q.
+__device__ __forceinline__ float sum9_rest(const float v[9], int q, const StepParams<float>& P) {
     return v[0] + ((((v[1] + v[3]) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8]))) +
-                   __fmul_rn((float)q, rest_lo_unit(v[0])));
+                   __fmul_rn((float)q, P.rest_unit));
 }
 
 // FP32 single-cell entry points used by every FP32 pseudopotential kernel (step, batch,
@@ -577,6 +612,21 @@ __device__ __forceinline__ void pp_collide(float v[9], float rho, float pc, cons
     pp_collide_v(vv, F1(rho), F1(pc), n, P);
 #pragma unroll
     for (int i = 0; i < 9; ++i) v[i] = vv[i].v;
+}
+
+// The same collision with a compensated rest population (v[0] and q updated together).
+__device__ __forceinline__ void pp_collide_comp(float v[9], int& q, float rho, float pc, const float pn[9],
+                                                const StepParams<float>& P) {
+    F1 vv[9], n[9], d0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        vv[i] = F1(v[i]);
+        n[i] = F1(pn[i]);
+    }
+    pp_collide_v<F1, true>(vv, F1(rho), F1(pc), n, P, &d0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) v[i] = vv[i].v;
+    rest_update(v[0], q, d0.v, P);
 }
 
 // FP32 single-cell entry points used by every FP32 free-energy kernel (the templates above
@@ -613,7 +663,7 @@ __device__ __forceinline__ void fe_collide_comp(float v[9], int& q, float rho, c
     fe_collide_v<F1, true>(vv, F1(rho), m, r, P, &d0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) v[i] = vv[i].v;
-    rest_update(v[0], q, d0.v);
+    rest_update(v[0], q, d0.v, P);
 }
 __device__ __forceinline__ float fe_mu(float rc, const float rn[9], const StepParams<float>& P) {
     // rn[0] is not used and callers need not set it
@@ -695,8 +745,14 @@ __global__ void __launch_bounds__(TX + 32) pp_step_kernel(const real* __restrict
             pn[7] = sm[sc - 1];
             pn[8] = sm[sc + 1];
             const real rho_c = sum9(prv);
-            pp_collide(prv, rho_c, pn[0], pn, P);
             const long long o = (long long)(r - 1) * nx + x;
+            if constexpr (std::is_same<real, float>::value) {
+                int q = rest_lo_plane(fin, pitch)[o];  // compensated rest population
+                pp_collide_comp(prv, q, rho_c, pn[0], pn, P);
+                rest_lo_plane(fout, pitch)[o] = (short)q;
+            } else {
+                pp_collide(prv, rho_c, pn[0], pn, P);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = prv[i];
         }
@@ -861,7 +917,7 @@ __device__ __forceinline__ void pull_cell(const real* __restrict__ S, long long 
 // stored as S_i(y) = f^eq_i(rho0(y + c_i)).
 template <typename real, typename src_t>
 __global__ void init_kernel(const src_t* __restrict__ rho0, real* __restrict__ S, int model, int nx, int ny,
-                            long long pitch) {
+                            long long pitch, float rest_inv) {
     const int cxs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int cys[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const long long n = (long long)nx * ny;
@@ -873,12 +929,14 @@ __global__ void init_kernel(const src_t* __restrict__ rho0, real* __restrict__ S
                 const real w = i == 0 ? real(4.0 / 9.0) : (i < 5 ? real(1.0 / 9.0) : real(1.0 / 36.0));
                 S[i * pitch + c] = w * (real)rho0[shifted_cell(x, y, cxs[i], cys[i], nx, ny)];
             }
+            if constexpr (std::is_same<real, float>::value)  // the rest population to ~40 bits
+                rest_lo_plane(S, pitch)[c] = rest_encode(4.0 / 9.0 * (double)rho0[c], S[c], rest_inv);
         } else {
             S[c] = (real)rho0[c];
 #pragma unroll
             for (int i = 1; i < 9; ++i) S[i * pitch + c] = real(0);
             if constexpr (std::is_same<real, float>::value)
-                rest_lo_plane(S, pitch)[c] = rest_encode(rho0[c], S[c]);
+                rest_lo_plane(S, pitch)[c] = rest_encode((double)rho0[c], S[c], rest_inv);
         }
     }
 }
@@ -895,7 +953,7 @@ __global__ void rho_kernel(const real* __restrict__ f, real* __restrict__ rho, r
         pull_cell(f, P.pitch, (int)(c % P.nx), (int)(c / P.nx), P.nx, P.ny, v);
         real r;
         if constexpr (std::is_same<real, float>::value)
-            r = model == 1 ? sum9_rest(v, rest_lo_plane(f, P.pitch)[c]) : sum9(v);
+            r = sum9_rest(v, rest_lo_plane(f, P.pitch)[c], P);
         else
             r = sum9(v);
         rho[c] = r;

@@ -276,11 +276,15 @@ __global__ void __launch_bounds__(TX + 32) pp_step_ext(const real* __restrict__ 
                 const real Fx = pn[0] * grad_x(pn) + P.fx;  // F_int,x + body force (Eq. 10)
                 wall_fill(prv, c != 0, real(-0.5) * Fx, real(-0.5) * P.fy);
             }
-            if (D.rho_ave)
-                pp_collide(prv, rho_prv, pn[0], pn, with_drive(P, D, x, rho_prv, s_rave));
-            else
-                pp_collide(prv, rho_prv, pn[0], pn, P);
             const long long o = (long long)c * nx + x;
+            const StepParams<real> Pd = D.rho_ave ? with_drive(P, D, x, rho_prv, s_rave) : P;
+            if constexpr (std::is_same<real, float>::value) {
+                int q = rest_lo_plane(fin, pitch)[o];  // compensated rest population
+                pp_collide_comp(prv, q, rho_prv, pn[0], pn, Pd);
+                rest_lo_plane(fout, pitch)[o] = (short)q;
+            } else {
+                pp_collide(prv, rho_prv, pn[0], pn, Pd);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * pitch + o] = prv[i];
         }
@@ -446,7 +450,7 @@ __global__ void rho_walls_kernel(const real* __restrict__ f, real* __restrict__ 
         if (!wjy && E.on && E.g != real(0) && (y == 0 || y == P.ny - 1)) wall_gravity_refill(v, y != 0, P, E);
         real r;
         if constexpr (std::is_same<real, float>::value)
-            r = model == 1 ? sum9_rest(v, rest_lo_plane(f, P.pitch)[c]) : sum9(v);
+            r = sum9_rest(v, rest_lo_plane(f, P.pitch)[c], P);
         else
             r = sum9(v);
         rho[c] = r;
@@ -730,7 +734,7 @@ __global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ 
                 int q = rest_lo_plane(fin, pitch)[o];
                 float d0;
                 fe_collide_iwb(p0, rho_c, mn, rn, un, vn, ext_fx(rho_c), ext_fy(rho_c) + fy_w, pg, P, E, &d0);
-                rest_update(p0[0], q, d0);
+                rest_update(p0[0], q, d0, P);
                 rest_lo_plane(fout, pitch)[o] = (short)q;
             } else {
                 fe_collide_iwb(p0, rho_c, mn, rn, un, vn, ext_fx(rho_c), ext_fy(rho_c) + fy_w, pg, P, E);
@@ -754,7 +758,7 @@ __global__ void __launch_bounds__(TX + 32) fe_step_iwb(const real* __restrict__ 
 // wall hold slots no step reads; the row is wrapped there).
 template <typename real, typename src_t>
 __global__ void init_iwb_kernel(const src_t* __restrict__ rho0, real* __restrict__ S, int nx, int ny,
-                                long long pitch, double pg_coef, double y_ref) {
+                                long long pitch, double pg_coef, double y_ref, float rest_inv) {
     const int cxs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int cys[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
@@ -770,7 +774,7 @@ __global__ void init_iwb_kernel(const src_t* __restrict__ rho0, real* __restrict
             const double f = i == 0 ? r - (1.0 - w[0]) * 3.0 * pg : w[i] * 3.0 * pg;
             S[i * pitch + c] = (real)f;
             if constexpr (std::is_same<real, float>::value)
-                if (i == 0) rest_lo_plane(S, pitch)[c] = rest_encode(f, (float)f);
+                if (i == 0) rest_lo_plane(S, pitch)[c] = rest_encode(f, (float)f, rest_inv);
         }
     }
 }

@@ -14,9 +14,10 @@
 // rows q-2..q; collide row q-2 with mu rows q-3..q-1 and rho rows q-3..q-1, re-pulling its
 // populations from staged rows q-3..q-1; release the stage of row q-3.
 //
-// The free-energy kernel also carries the compensated rest population (rest_update in
-// lbm_kernels.cuh): each lane reads and writes one 32-bit word of the int16 rest plane per
-// row (its two cells), loaded when the row is pulled and used two iterations later.
+// Both kernels carry the compensated rest population (rest_update in lbm_kernels.cuh): each
+// lane reads and writes one 32-bit word of the int16 rest plane per row (its two cells),
+// loaded when the row is pulled and used when that row is collided (two iterations later for
+// the free-energy kernel, one for the pseudopotential kernel).
 //
 // Requirements (checked on the host): nx % 4 == 0, nx >= 8, ny >= 4; every wait bounded.
 #pragma once
@@ -160,17 +161,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
             neighbours_pair(r3, r2, r1, rn);
             F2 d0;
             fe_collide_v<F2, true>(v, r2.c, mn, rn, P, &d0);
-            // compensated rest population of both cells (rest_update)
-            int qa = (int)(short)(ql2 & 0xffffu), qb = (int)ql2 >> 16;
-            float ha = v[0].v.x, hb = v[0].v.y;
-            rest_update(ha, qa, d0.v.x);
-            rest_update(hb, qb, d0.v.y);
-            v[0] = F2(ha, hb);
+            const unsigned qw = rest_update_pair(v[0], ql2, d0, P);  // compensated rest population
             const long long oc = (long long)(q - 2) * nx + x0 + col;
             float* o = fout + oc;
 #pragma unroll
             for (int i = 0; i < 9; ++i) *reinterpret_cast<float2*>(o + i * P.pitch) = v[i].v;
-            qout[oc >> 1] = ((unsigned)qa & 0xffffu) | ((unsigned)qb << 16);
+            qout[oc >> 1] = qw;
         }
         // row q-3 (ring index k-4) is no longer read by this warp
         __syncwarp();
@@ -230,6 +226,11 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
     const bool out = act && lane >= 1 && 2 * lane <= nw;
     const int sc = col + 4;
     Row2 p1, p2;  // psi of rows q-1, q-2
+    // rest-population extensions q (two int16 per lane) of rows q and q-1: loaded when row q is
+    // pulled, used by its collision in the next iteration
+    const unsigned* qin = reinterpret_cast<const unsigned*>(rest_lo_plane(fin, P.pitch));
+    unsigned* qout = reinterpret_cast<unsigned*>(rest_lo_plane(fout, P.pitch));
+    unsigned ql0 = 0, ql1 = 0;
     p1.c = p2.c = F2::c(0.0f);
     p1.L = p1.R = p2.L = p2.R = 0.0f;
     F2 rho1 = F2::c(1.0f);  // rho of row q-1
@@ -239,6 +240,7 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
         const int k = q + 1 - rbase;  // ring index of row q+1
         ok = mbar_wait_bounded(&sm.full[k % S], (uint32_t)((k / S) & 1));
         if (!ok) break;
+        if (out && q >= y0 && q < y1) ql0 = __ldg(qin + (((long long)q * nx + x0 + col) >> 1));
         F2 rho0 = F2::c(1.0f), psi = F2::c(0.0f);
         if (act) {
             F2 v[9];
@@ -252,10 +254,14 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
             F2 v[9], pn[9];
             pull_pair<W8>(sm.stage[(k - 3) % S], sm.stage[(k - 2) % S], sm.stage[(k - 1) % S], sc, v);
             neighbours_pair(p2, p1, p0, pn);
-            pp_collide_v(v, rho1, pn[0], pn, P);
-            float* o = fout + (long long)(q - 1) * nx + x0 + col;
+            F2 d0;
+            pp_collide_v<F2, true>(v, rho1, pn[0], pn, P, &d0);
+            const unsigned qw = rest_update_pair(v[0], ql1, d0, P);  // compensated rest population
+            const long long oc = (long long)(q - 1) * nx + x0 + col;
+            float* o = fout + oc;
 #pragma unroll
             for (int i = 0; i < 9; ++i) *reinterpret_cast<float2*>(o + i * P.pitch) = v[i].v;
+            qout[oc >> 1] = qw;
         }
         // row q-2 (ring index k-3) is no longer read by this warp
         __syncwarp();
@@ -263,6 +269,7 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
         p2 = p1;
         p1 = p0;
         rho1 = rho0;
+        ql1 = ql0;
     }
     if (!ok) atomicExch(err, 1);
 }

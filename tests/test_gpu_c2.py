@@ -1,0 +1,84 @@
+"""The static-droplet configuration in full, FP32 on the GPU against the FP64 oracle.
+
+256 x 256 periodic lattice, Carnahan-Starling a = 0.25 (the droplet value of Sec. 5.2), Tr in
+{0.9, 0.8, 0.7} x R in {20, 30, 40, 60}, tau = 1, both models (free energy with kappa = 0.5;
+pseudopotential with kappa_P, kappa_Li matched to that width and surface tension, Sec. 3),
+tanh droplets of width 5 started at rest, FP32 populations, 2e4 steps (Laplace test of Sec.
+5.2, Eq. 25; Eq. S18 in 2-D).
+
+At step 1e4 every droplet is compared with the oracle run from the same input: density cell
+by cell within 1e-5 (the static bar), the pressure jump relative to itself within 1e-3, and
+the largest spurious velocity within 1% of the oracle's (or within the FP32 velocity floor of
+1e-6 where the oracle's is below it).  At step 2e4 the pressure jumps of the four radii follow
+the Laplace law: linear in 1/R with the surface tension of the planar profile (Eqs. 25-26)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import observables as OO
+from oracle import thermo
+from paper_2403_11167_gb300 import inputs
+from helpers import gpu_context, oracle_params, rho_err
+
+pytestmark = pytest.mark.gpu
+
+PP, FE = 0, 1
+A, KAPPA, L = 0.25, 0.5, 256
+RADII = (20.0, 30.0, 40.0, 60.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("Tr", [0.9, 0.8, 0.7])
+@pytest.mark.parametrize("model", [PP, FE])
+def test_static_droplets_fp32_against_oracle(model, Tr):
+    from paper_2403_11167_gb300 import lbm
+
+    kw = dict(a=A, Tr=Tr, tau_nu=1.0)
+    kw.update({"match_kappa": KAPPA} if model == PP else {"kappa": KAPPA})
+    rows, late = [], []
+    for R in RADII:
+        ctx, rp, th = gpu_context(model, lbm.LBM_F32, L, L, **kw)
+        rho0 = inputs.droplet(L, L, R, th.rho_v, th.rho_l)
+        ctx.set_density(rho0)
+        ctx.step(10000)
+        rho, ux, uy = ctx.fields()
+        obs = ctx.observables(lbm.DROPLET)
+        op = oracle_params(rp, th)
+        rr, uxr, uyr, *_ = O.macro(model, op, O.run(model, op, O.init(model, rho0), 10000))
+        ref = OO.observables(rr, uxr, uyr, 1, rp.a, rp.b, rp.R, th.T)
+        rows.append((R, rho_err(rho, rr), obs["dp"] / ref["dp"] - 1, obs["u_max"], ref["u_max"], obs["radius"]))
+        ctx.step(10000)
+        late.append(ctx.observables(lbm.DROPLET))
+        ctx.close()
+    for R, e, edp, u, uref, _ in rows:
+        print(f"model {model} Tr {Tr} R {R}: rho_err {e:.2e}  dp {edp:+.2e}  u_max {u:.3e} (oracle {uref:.3e})")
+    for R, e, edp, u, uref, _ in rows:
+        assert e < 1e-5, (R, e)
+        assert abs(edp) < 1e-3, (R, edp)
+        assert abs(u - uref) <= max(1e-2 * uref, 1e-6), (R, u, uref)
+    # Laplace law at 2e4 steps: dp linear in 1/R_equimolar, slope the planar surface tension.
+    # Only droplets that are still static enter the fit: near the critical point (Tr = 0.9) the
+    # vapour of the 256^2 box can absorb a small droplet, which then evaporates (Kelvin effect:
+    # the droplet's vapour pressure exceeds that of the Maxwell vapour it starts in).
+    assert all(o["status"] == lbm.LBM_OK for o in late)
+    for R, o in zip(RADII, late):
+        print(f"model {model} Tr {Tr} R {R} at 2e4: radius {o['radius']:.3f} dp {o['dp']:.4e} u_max {o['u_max']:.2e}")
+    # static: the equimolar radius moved by less than 2% from step 1e4 to 2e4
+    alive = [(R, o) for (R, *_, r1), o in zip(rows, late) if abs(o["radius"] / r1 - 1) < 0.02]
+    gone = [R for (R, *_), o in zip(rows, late) if all(R != a for a, _ in alive)]
+    assert len(alive) >= 3 and all(R <= 20 for R in gone), gone
+    inv = np.array([1.0 / o["radius"] for _, o in alive])
+    dp = np.array([o["dp"] for _, o in alive])
+    (slope, icpt), *_ = np.linalg.lstsq(np.column_stack([inv, np.ones_like(inv)]), dp, rcond=None)
+    gamma = thermo.fe_surface_tension(A, 4.0, 1.0, Tr, KAPPA)
+    print(f"model {model} Tr {Tr}: {len(alive)} static droplets, Laplace slope / gamma = {slope / gamma:.4f}, "
+          f"intercept / dp = {icpt / dp[0]:+.4f}")
+    assert np.all(np.diff(dp) < 0)
+    assert abs(slope / gamma - 1) < 0.06, slope / gamma
+    assert abs(icpt) < 0.06 * dp[0], icpt / dp[0]
