@@ -29,10 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "D2Q9 multiphase MLUPS & HBM-roofline fraction; sweep runs/s batched vs plain"
-# Algorithmic bytes per FP32 cell update: the state each step must read and write once.
-# Pseudopotential: 9 FP32 populations in, 9 out (72 B).  Free energy: the same plus the int16
-# extension of the rest population (compensated f_0), in and out (76 B).
-BYTES_PER_CELL = {0: 72, 1: 76}
+# Algorithmic bytes per FP32 cell update: the state each step must read and write once, 9 FP32
+# populations and the int16 extension of the rest population (compensated f_0), in and out:
+# 2 x (36 + 2) = 76 B for both models.
+BYTES_PER_CELL = {0: 76, 1: 76}
 
 
 def parse():
@@ -251,6 +251,21 @@ def run_sweep(args):
     t_batch = time.perf_counter() - t
     diverged = sum(1 for o in obs if o["status"] != 0)
     b.close()
+    # floor of the tiled path's per-step launches (graph replays of one launch per step): a
+    # single tiled lattice too small to do measurable work, 2e4 steps
+    e = inputs.calibration_sweep(1, seed=5)[0]
+    e.update(geometry=0, nx=512, ny=12, radius=0.0, nsteps=20000, Tr=0.8, kappa_P=1.0)
+    fspecs, frhos = lbm.sweep_specs([e])
+    fb = lbm.Batch(fspecs, frhos)
+    assert fb.info()["n_resident"] == 0
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    fb.run()
+    fb.observables()
+    floor_s = (time.perf_counter() - t) / 20000
+    fb.close()
+    # lattices of more than 4452 cells run tiled (lbm_batch_create's residency rule)
+    max_tiled = max((s["nsteps"] for s in specs if s["nx"] * s["ny"] > 4452), default=0)
     ctxs = [lbm.Context(s["params"], s["nx"], s["ny"]) for s in specs]
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -262,10 +277,19 @@ def run_sweep(args):
     for ctx in ctxs:
         ctx.close()
     n = len(specs)
+    ok = n - diverged
     return {"lattices": n, "cell_updates": cells, "batched_s": t_batch, "plain_s": t_plain,
+            # every lattice runs all its steps on both paths (a diverged one is only flagged at
+            # the end), so runs/s counts all of them; the completed (non-diverged) runs per
+            # second are reported beside them
             "batched_runs_per_s": n / t_batch, "plain_runs_per_s": n / t_plain, "speedup": t_plain / t_batch,
+            "completed_lattices": ok, "diverged_lattices": diverged,
+            "batched_completed_runs_per_s": ok / t_batch, "plain_completed_runs_per_s": ok / t_plain,
             "batched_mlups": cells / t_batch / 1e6, "plain_mlups": cells / t_plain / 1e6,
-            "diverged_lattices": diverged, "resident_lattices": info["n_resident"],
+            "tiled_step_floor_us": floor_s * 1e6, "tiled_steps": max_tiled,
+            # upper bound of what one persistent launch could save over the per-step replays
+            "tiled_launch_floor_fraction": floor_s * max_tiled / t_batch,
+            "resident_lattices": info["n_resident"],
             "tiled_work_items": info["n_items"], "resident_threads": info["resident_threads"],
             "strip_rows": info["strip_rows"],
             "workload": "512 seeded pseudopotential calibration lattices (64x4..512x512 slabs and droplets, "
@@ -434,6 +458,13 @@ def run_surrogate(args):
         "held_out_sets": len(ho), "held_out_valid": int(okh.sum()), "held_out_with_sigma": int(sig.sum()),
         "max_rel_err": {"rho_l": float(err[:, 0].max()), "rho_v": float(err[:, 1].max()),
                         "width": float(err[:, 2].max()), "sigma": float(err[sig, 3].max())},
+        # per width factor: sets with a sigma label and their largest sigma error (sigma's domain
+        # is kappa_P >= 0.7; kappa_P = 0.4 calibration droplets mostly diverge)
+        "sigma_by_kappa_P": {f"{k:g}": {"held_out_valid": int((Xh[okh, 3] == k).sum()),
+                                        "with_sigma": int((sig & (Xh[okh, 3] == k)).sum()),
+                                        "max_rel_err": (float(err[sig & (Xh[okh, 3] == k), 3].max())
+                                                        if (sig & (Xh[okh, 3] == k)).any() else None)}
+                             for k in (0.4, 0.7, 1.0)},
         "mean_rel_err": {"rho_l": float(err[:, 0].mean()), "rho_v": float(err[:, 1].mean()),
                          "width": float(err[:, 2].mean()), "sigma": float(err[sig, 3].mean())},
         "gain_rho_v_Tr_le_0.6": {"sets": int(low.sum()), "theory_mean_rel_err": float(e_th.mean()),

@@ -132,6 +132,16 @@ int lbm_params_default(int model, lbm_params* p);
  * of the free-energy equilibrium, Eq. 20; the free-energy model accepts it). */
 int lbm_resolve_params(const lbm_params* in, lbm_params* out, lbm_thermo* th);
 
+/* Host-only: thermodynamically consistent densities of a 2-D droplet of radius `radius` and
+ * surface tension `gamma` (Sec. 5.2, Fig. 5 discussion: the vapour density a droplet should
+ * have): equal chemical potential in both phases (Eq. 29) and p(rho_l) - p(rho_v) =
+ * gamma / radius (Laplace's law in 2-D), Carnahan-Starling EOS (Eq. 28) at temperature T.
+ * *rho_v, *rho_l: in, the starting pair (normally the planar Maxwell densities); out, the
+ * solution (Newton's method, steps down to the rounding level).  Errors: LBM_ERR_ARG for invalid
+ * inputs, LBM_ERR_NOCONVERGE if Newton leaves 0 < rho_v < rho_l or does not converge. */
+int lbm_kelvin_2d(double a, double b, double R, double T, double gamma, double radius, double* rho_v,
+                  double* rho_l);
+
 /* Host-only: lbm_resolve_params on each of in[0..n-1], spread over the host's cores
  * (std::thread); identical inputs are resolved once.  status[i] receives each item's
  * return code (out[i], th[i] are valid where it is LBM_OK).  Returns LBM_ERR_ARG for
@@ -316,7 +326,11 @@ const char* lbm_batch_last_error(void);
 /* it replaces the preliminary calibration runs of Secs. 5.1-5.2).  An MLP 4 -> 128 ->   */
 /* 128 -> 128 -> 4 with GELU maps X = (Tr, a, b, kappa_P) to Y = (rho_l, rho_v, W,       */
 /* sigma) as measured by calibration runs (flat interface: rho_l, rho_v, W; Laplace fit */
-/* of droplets: sigma).  Internally X and (rho_l, ln rho_v, W, sigma) are standardised  */
+/* of droplets: sigma).  Domain of sigma: kappa_P >= 0.7.  At kappa_P = 0.4 the         */
+/* calibration droplets carry large spurious currents and most diverge, so there are no  */
+/* sigma labels and the sigma output there is an extrapolation, not a calibrated value;  */
+/* rho_l, rho_v and W are trained for every kappa_P.                                    */
+/* Internally X and (rho_l, ln rho_v, W, sigma) are standardised                        */
 /* with stats16 = {mean X[4], std X[4], mean Y'[4], std Y'[4]} (Y' with ln rho_v).      */
 /* Parameters: 34,180 FP32 values, per layer l = 0..3 the weights W_l [out][in]          */
 /* (row-major) followed by the bias b_l.  Training: full-batch MSE in the standardised  */

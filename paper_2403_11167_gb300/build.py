@@ -21,23 +21,45 @@ def _obj(src):
     return os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
 
 
+def _stamp(src):
+    return _obj(src) + ".flags"
+
+
+def _cmd(src, obj):
+    return [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *EXTRA,
+            "-c", os.path.join(CSRC, src), "-o", obj]
+
+
 def _deps_newer(obj, src):
     if not os.path.exists(obj):
+        return True
+    try:  # rebuild when the compile flags changed
+        with open(_stamp(src)) as f:
+            if f.read() != " ".join(_cmd(src, obj)):
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(obj)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "lbm.h")]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+# Extra nvcc flags for tuning builds (e.g. LBM_NVCC_EXTRA="-DLBM_FEP_STAGES=8"); the default
+# build uses none.
+EXTRA = os.environ.get("LBM_NVCC_EXTRA", "").split()
+
+
 def _compile(src, verbose):
     obj = _obj(src)
-    cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
-           os.path.join(CSRC, src), "-o", obj]
+    cmd = _cmd(src, obj)
+    stamp = " ".join(cmd)
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    with open(_stamp(src), "w") as f:
+        f.write(stamp)
     return r.stderr
 
 

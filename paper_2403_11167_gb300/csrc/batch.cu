@@ -555,6 +555,12 @@ extern "C" int lbm_batch_create(int n, const lbm_batch_lattice* specs, const dou
         P.fy = (float)rp.body_fy;
         P.rest_unit = (float)lbm_host::rest_unit(rp.b);
         P.rest_inv = (float)lbm_host::rest_inv(rp.b);
+        P.h_e = (float)(1.0 - 0.5 / rp.tau_e);
+        P.h_z = (float)(1.0 - 0.5 / rp.tau_zeta);
+        P.h_q = (float)(1.0 - 0.5 / rp.tau_q);
+        P.h_nu = (float)(1.0 - 0.5 / rp.tau_nu);
+        P.h6_e = (float)(6.0 * (1.0 - 0.5 / rp.tau_e));
+        P.h6_z = (float)(6.0 * (1.0 - 0.5 / rp.tau_zeta));
         L.RT = rp.R * th.T;
         L.a = rp.a;
         L.b4 = 0.25 * rp.b;

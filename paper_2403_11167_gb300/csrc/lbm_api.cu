@@ -50,7 +50,7 @@ constexpr int kRedBlocks = 304;  // observables partial-reduction blocks (2 x 15
 #define LBM_PPP_STAGES 6
 #endif
 #ifndef LBM_FEP_STAGES
-#define LBM_FEP_STAGES 6
+#define LBM_FEP_STAGES 8
 #endif
 constexpr int kPPPWarps = 4;
 constexpr int kPPPStages = LBM_PPP_STAGES;
@@ -255,6 +255,13 @@ extern "C" int lbm_resolve_params(const lbm_params* in, lbm_params* out, lbm_the
     return LBM_OK;
 }
 
+extern "C" int lbm_kelvin_2d(double a, double b, double R, double T, double gamma, double radius, double* rho_v,
+                             double* rho_l) {
+    if (!rho_v || !rho_l || !(a > 0 && b > 0 && R > 0 && T > 0)) return LBM_ERR_ARG;
+    const lbm_host::CS eos{a, b, R};
+    return lbm_host::kelvin_2d(eos, T, gamma, radius, rho_v, rho_l);
+}
+
 extern "C" int lbm_resolve_params_many(int n, const lbm_params* in, lbm_params* out, lbm_thermo* th, int* status) {
     if (n < 0 || (n > 0 && (!in || !out || !th || !status))) return LBM_ERR_ARG;
     // identical inputs (byte-wise) are resolved once and copied
@@ -347,6 +354,12 @@ static void fill_step_params(lbmk::StepParams<real>& s, const lbm_ctx* c) {
     s.fy = (real)p.body_fy;
     s.rest_unit = (real)lbm_host::rest_unit(p.b);
     s.rest_inv = (real)lbm_host::rest_inv(p.b);
+    s.h_e = (real)(1.0 - 0.5 / p.tau_e);
+    s.h_z = (real)(1.0 - 0.5 / p.tau_zeta);
+    s.h_q = (real)(1.0 - 0.5 / p.tau_q);
+    s.h_nu = (real)(1.0 - 0.5 / p.tau_nu);
+    s.h6_e = (real)(6.0 * (1.0 - 0.5 / p.tau_e));
+    s.h6_z = (real)(6.0 * (1.0 - 0.5 / p.tau_zeta));
 }
 
 static int choose_rows(int nx, int ny, int tx, int strips_per_sm) {

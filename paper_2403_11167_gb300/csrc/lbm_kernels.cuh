@@ -38,6 +38,10 @@ struct StepParams {
     real s_e, s_z, s_q, s_nu;  // relaxation rates 1/tau (Eq. 3); tau_rho, tau_j drop out
     real fx, fy;       // body force
     real rest_unit, rest_inv;  // FP32: unit of the rest population's extension and its inverse
+    // 1 - s/2 of e, zeta, q, nu and 6 (1 - s/2) of e, zeta (forcing factors of Eq. 1), rounded
+    // once on the host: computed in the kernels, a compiler may fuse them differently in two
+    // kernels and the same cell would then differ by an ulp of the increments between routes
+    real h_e, h_z, h_q, h_nu, h6_e, h6_z;
 };
 
 // Correctly rounded reciprocal (FP32: one hardware-assisted sequence instead of a full division).
@@ -282,7 +286,9 @@ struct F1 {
 };
 __device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1(__fadd_rn(a.v, b.v)); }
 __device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1(__fsub_rn(a.v, b.v)); }
-__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1(__fmul_rn(a.v, b.v)); }
+// a product is a fused multiply-add with +0 (the rounded product, a zero product taken as +0),
+// for the reason given at F2
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1(__fmaf_rn(a.v, b.v, 0.0f)); }
 __device__ __forceinline__ F1 operator-(F1 a) { return F1(-a.v); }
 __device__ __forceinline__ F1 fmav(F1 a, F1 b, F1 c) { return F1(__fmaf_rn(a.v, b.v, c.v)); }
 
@@ -293,10 +299,17 @@ struct F2 {
     __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
     static __device__ __forceinline__ F2 c(float s) { return F2(s, s); }
 };
+// Packed FP32 (one instruction for both lanes).  The packed add and fused multiply-add round
+// like their scalar _rn counterparts, but a packed multiply whose only use is a packed add is
+// fused with it by the compiler -- whatever the rounding modifier or -fmad setting -- where the
+// scalar __fmul_rn never is, so the one-cell and two-cell instantiations of the step rounded
+// differently.  A product is therefore a fused multiply-add with +0, which no compiler may
+// treat as a multiply (it maps a -0 product to +0), in both types; the arithmetic writes fmav
+// wherever it wants a product fused into a sum.
 __device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
 __device__ __forceinline__ F2 operator-(F2 a) { return F2(-a.v.x, -a.v.y); }
 __device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__fadd2_rn(a.v, (-b).v)); }
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__ffma2_rn(a.v, b.v, make_float2(0.0f, 0.0f))); }
 __device__ __forceinline__ F2 fmav(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
 
 // Eq. (29) relative to the coexistence reference (see mu_bulk_rel), one cell, explicit ops.
@@ -437,8 +450,7 @@ __device__ __forceinline__ void fe_collide_v(F v[9], F rho, const F mn[9], const
     const F s = fmav(ux, grx, uy * gry);                                      // u . grad rho
     const F Gx = fmav(grx, F::c(1.0f / 3.0f), Fx), Gy = fmav(gry, F::c(1.0f / 3.0f), Fy);  // F + c_s^2 grad rho
     const F fe = fmav(F::c(6.0f), uF, F::c(4.0f) * s);
-    const float he = 1.0f - 0.5f * P.s_e, hz = 1.0f - 0.5f * P.s_z, hq = 1.0f - 0.5f * P.s_q,
-                hn = 1.0f - 0.5f * P.s_nu;
+    const float he = P.h_e, hz = P.h_z, hq = P.h_q, hn = P.h_nu;
     // e - e^eq = (-4 f0 - sax + 2 sdg) - rho (3 uu - 4) and zeta - zeta^eq = (4 f0 - 2 sax + sdg)
     // - rho (4 - 3 uu) with rho = f0 + sax + sdg: f0 cancels exactly
     const F rhouu = F::c(3.0f) * rho * uu;
@@ -507,11 +519,10 @@ __device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9],
     const F uu = fmav(ux, ux, uy * uy);
     const F uF = fmav(ux, Fx, uy * Fy);
     const F Ls = fmav(F::c(1.5f), Qxx + Qyy, L);  // L + 1.5 tr Q
-    const float he = 1.0f - 0.5f * P.s_e, hz = 1.0f - 0.5f * P.s_z, hq = 1.0f - 0.5f * P.s_q,
-                hn = 1.0f - 0.5f * P.s_nu;
+    const float hq = P.h_q, hn = P.h_nu;
     // m* - m = -L (m - m^eq) + (I - L/2) MF' + MC  (Eqs. 1, 4/S66, 32, 13)
-    const F de = fmav(F::c(6.0f * he), uF, fmav(F::c(P.s_e), Ls, F::c(-P.s_e) * (e - rho * fmav(F::c(3.0f), uu, F::c(-2.0f)))));
-    const F dz = fmav(F::c(-6.0f * hz), uF, fmav(F::c(-P.s_z), Ls, F::c(-P.s_z) * (z - rho * fmav(F::c(-3.0f), uu, F::c(1.0f)))));
+    const F de = fmav(F::c(P.h6_e), uF, fmav(F::c(P.s_e), Ls, F::c(-P.s_e) * (e - rho * fmav(F::c(3.0f), uu, F::c(-2.0f)))));
+    const F dz = fmav(F::c(-P.h6_z), uF, fmav(F::c(-P.s_z), Ls, F::c(-P.s_z) * (z - rho * fmav(F::c(-3.0f), uu, F::c(1.0f)))));
     const F dqx = fmav(F::c(-hq), Fx, F::c(-P.s_q) * fmav(rho, ux, qx));
     const F dqy = fmav(F::c(-hq), Fy, F::c(-P.s_q) * fmav(rho, uy, qy));
     const F dpxx = fmav(F::c(2.0f * hn), fmav(ux, Fx, -(uy * Fy)),
@@ -541,9 +552,17 @@ __device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9],
 // step reads hi only (rho = sum f_i in FP32); the observables and the host population views
 // add q u.
 
-// (hi + qf u) + d -> (hi, qf), qf the extension held as an (integer-valued) float: TwoSum of
-// hi and d, the old extension carried in the error term, Fast2Sum renormalisation, qf the
-// residual rounded to a multiple of u.  Written once for one cell (F1) or two (F2).
+// Nearest integer of each lane (the packed unit has no rounding instruction).
+__device__ __forceinline__ F1 rint_v(F1 x) { return F1(rintf(x.v)); }
+__device__ __forceinline__ F2 rint_v(F2 x) { return F2(rintf(x.v.x), rintf(x.v.y)); }
+
+// (hi + qf u) + d -> (hi, qf), qf the extension held as an integer-valued float: TwoSum of hi
+// and d, the old extension carried in the error term, Fast2Sum renormalisation, the residual
+// rounded to a multiple of u.  The pair is then made canonical -- hi the FP32 value nearest to
+// hi + qf u, ties to even -- so that a host round trip through FP64 (lbm_get_populations /
+// lbm_set_populations, checkpoints) restores it bit for bit: rounding the residual can carry
+// |qf u| up to u/2 past half an ulp of hi, and the last fused multiply-add moves that excess
+// (a whole ulp, an exact multiple of u) into hi.  Written once for one cell (F1) or two (F2).
 template <class F>
 __device__ __forceinline__ void rest_update_v(F& hi, F& qf, F d, const StepParams<float>& P) {
     const F lo = qf * F::c(P.rest_unit);
@@ -553,8 +572,10 @@ __device__ __forceinline__ void rest_update_v(F& hi, F& qf, F d, const StepParam
     const F t = err + lo;
     const F h2 = s + t;
     const F l2 = t - (h2 - s);  // s + t = h2 + l2
-    hi = h2;
-    qf = l2 * F::c(P.rest_inv);
+    const F q2 = rint_v(l2 * F::c(P.rest_inv));
+    const F h3 = fmav(q2, F::c(P.rest_unit), h2);  // nearest FP32 to h2 + q2 u
+    qf = fmav(h2 - h3, F::c(P.rest_inv), q2);      // exact: h2 - h3 is 0 or one ulp
+    hi = h3;
 }
 
 // Extension <-> int16 storage (rounded to nearest, clamped to +-32767).

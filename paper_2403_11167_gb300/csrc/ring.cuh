@@ -156,6 +156,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
         : "memory");
 }
 
+// Per-thread asynchronous 4-byte copy global -> shared (cp.async, L1-allocating) and its
+// group bookkeeping.  A thread sees its own copies in shared memory after cp.async.wait_group;
+// no other thread reads them, so no barrier is needed.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 template <int NW, int S, int TXW>
 struct WarpStripSmem {
     static constexpr int TX = NW * TXW;  // widest strip
@@ -163,6 +175,11 @@ struct WarpStripSmem {
     float stage[S][9 * W8];
     uint64_t full[S];
     uint64_t empty[S];
+    // rest-population extensions (two int16 per lane) of the last three pulled rows, each lane
+    // its own word: copied asynchronously when a row is pulled and read by the same lane when
+    // that row is collided one (pseudopotential) or two (free energy) rows later, so that no
+    // register waits on the global load in between
+    uint32_t qext[3][NW][32];
 };
 
 // Strip geometry shared by the host and the kernels: nx is split into gx strips of equal

@@ -123,11 +123,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
     const int sc = col + 4;
     Row2 r1, r2, r3;  // rho of rows q-1, q-2, q-3
     Row2 m2, m3;      // mu of rows q-2, q-3
-    // rest-population extensions q (two int16 per lane) of rows q, q-1, q-2: loaded when row q
-    // is pulled, used two iterations later by its collision
+    // rest-population extensions q (two int16 per lane): copied into slot (row mod 3) of the
+    // lane's qext ring when the row is pulled, read two iterations later by its collision
     const unsigned* qin = reinterpret_cast<const unsigned*>(rest_lo_plane(fin, P.pitch));
     unsigned* qout = reinterpret_cast<unsigned*>(rest_lo_plane(fout, P.pitch));
-    unsigned ql0 = 0, ql1 = 0, ql2 = 0;
     r1.c = r2.c = r3.c = m2.c = m3.c = F2::c(1.0f);
     r1.L = r1.R = r2.L = r2.R = r3.L = r3.R = m2.L = m2.R = m3.L = m3.R = 1.0f;
     bool ok = mbar_wait_bounded(&sm.full[0], 0) && mbar_wait_bounded(&sm.full[1], 0);
@@ -136,7 +135,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
         const int k = q + 1 - rbase;  // ring index of row q+1
         ok = mbar_wait_bounded(&sm.full[k % S], (uint32_t)((k / S) & 1));
         if (!ok) break;
-        if (out && q >= y0 && q < y1) ql0 = __ldg(qin + (((long long)q * nx + x0 + col) >> 1));
+        if (out && q >= y0 && q < y1)
+            cp_async4(&sm.qext[(q - y0 + 3) % 3][warp][lane], qin + (((long long)q * nx + x0 + col) >> 1));
+        cp_async_commit();
         // pull row q, rho(q)
         F2 rho0 = F2::c(1.0f);
         if (act) {
@@ -161,6 +162,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
             neighbours_pair(r3, r2, r1, rn);
             F2 d0;
             fe_collide_v<F2, true>(v, r2.c, mn, rn, P, &d0);
+            cp_async_wait<2>();  // the copy of row q-2's extensions (two groups ago) has landed
+            const unsigned ql2 = sm.qext[(q - 2 - y0 + 3) % 3][warp][lane];
             const unsigned qw = rest_update_pair(v[0], ql2, d0, P);  // compensated rest population
             const long long oc = (long long)(q - 2) * nx + x0 + col;
             float* o = fout + oc;
@@ -176,9 +179,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
         r1 = r0;
         m3 = m2;
         m2 = m1;
-        ql2 = ql1;
-        ql1 = ql0;
     }
+    cp_async_wait<0>();
     if (!ok) atomicExch(err, 1);
 }
 
@@ -226,11 +228,10 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
     const bool out = act && lane >= 1 && 2 * lane <= nw;
     const int sc = col + 4;
     Row2 p1, p2;  // psi of rows q-1, q-2
-    // rest-population extensions q (two int16 per lane) of rows q and q-1: loaded when row q is
-    // pulled, used by its collision in the next iteration
+    // rest-population extensions q (two int16 per lane): copied into slot (row mod 3) of the
+    // lane's qext ring when the row is pulled, read by its collision in the next iteration
     const unsigned* qin = reinterpret_cast<const unsigned*>(rest_lo_plane(fin, P.pitch));
     unsigned* qout = reinterpret_cast<unsigned*>(rest_lo_plane(fout, P.pitch));
-    unsigned ql0 = 0, ql1 = 0;
     p1.c = p2.c = F2::c(0.0f);
     p1.L = p1.R = p2.L = p2.R = 0.0f;
     F2 rho1 = F2::c(1.0f);  // rho of row q-1
@@ -240,7 +241,9 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
         const int k = q + 1 - rbase;  // ring index of row q+1
         ok = mbar_wait_bounded(&sm.full[k % S], (uint32_t)((k / S) & 1));
         if (!ok) break;
-        if (out && q >= y0 && q < y1) ql0 = __ldg(qin + (((long long)q * nx + x0 + col) >> 1));
+        if (out && q >= y0 && q < y1)
+            cp_async4(&sm.qext[(q - y0 + 3) % 3][warp][lane], qin + (((long long)q * nx + x0 + col) >> 1));
+        cp_async_commit();
         F2 rho0 = F2::c(1.0f), psi = F2::c(0.0f);
         if (act) {
             F2 v[9];
@@ -256,6 +259,8 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
             neighbours_pair(p2, p1, p0, pn);
             F2 d0;
             pp_collide_v<F2, true>(v, rho1, pn[0], pn, P, &d0);
+            cp_async_wait<1>();  // the copy of row q-1's extensions (one group ago) has landed
+            const unsigned ql1 = sm.qext[(q - 1 - y0 + 3) % 3][warp][lane];
             const unsigned qw = rest_update_pair(v[0], ql1, d0, P);  // compensated rest population
             const long long oc = (long long)(q - 1) * nx + x0 + col;
             float* o = fout + oc;
@@ -269,8 +274,8 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
         p2 = p1;
         p1 = p0;
         rho1 = rho0;
-        ql1 = ql0;
     }
+    cp_async_wait<0>();
     if (!ok) atomicExch(err, 1);
 }
 

@@ -217,4 +217,34 @@ int pp_theory(const CS& eos, double T, double rv, double rl, double p0, double e
     return (std::isfinite(*width) && std::isfinite(*gamma)) ? LBM_OK : LBM_ERR_NOCONVERGE;
 }
 
+// A droplet of radius r in its own vapour: mu_b(rho_v) = mu_b(rho_l) and p(rho_l) - p(rho_v) =
+// gamma / r (2-D Laplace law).  Newton's method on the two residuals from the planar pair, with
+// d mu_b / d rho = p'(rho) / rho (Gibbs-Duhem at constant T); converged when the Newton steps
+// reach the rounding level of the residuals (1e-13 relative).
+int kelvin_2d(const CS& eos, double T, double gamma, double radius, double* rho_v, double* rho_l) {
+    if (!(radius > 0) || !std::isfinite(gamma) || !(*rho_v > 0) || !(*rho_l > *rho_v)) return LBM_ERR_ARG;
+    double rv = *rho_v, rl = *rho_l;
+    double last_v = 1.0, last_l = 1.0;  // relative size of the last Newton step
+    for (int it = 0; it < 60; ++it) {
+        const double f1 = eos.mu(rl, T) - eos.mu(rv, T);
+        const double f2 = eos.p(rl, T) - eos.p(rv, T) - gamma / radius;
+        const double pv = eos.dp(rv, T), pl = eos.dp(rl, T);
+        const double j11 = -pv / rv, j12 = pl / rl, j21 = -pv, j22 = pl;
+        const double det = j11 * j22 - j12 * j21;
+        if (!(std::fabs(det) > 0)) return LBM_ERR_NOCONVERGE;
+        const double dv = (-f1 * j22 + f2 * j12) / det, dl = (-j11 * f2 + j21 * f1) / det;
+        rv += dv;
+        rl += dl;
+        if (!(rv > 0) || !(rl > rv)) return LBM_ERR_NOCONVERGE;
+        last_v = std::fabs(dv) / rv;
+        last_l = std::fabs(dl) / rl;
+        if (last_v <= 1e-15 && last_l <= 1e-15) break;
+    }
+    // quadratic convergence ends in steps at the rounding level of the residuals
+    if (!(last_v <= 1e-13 && last_l <= 1e-13)) return LBM_ERR_NOCONVERGE;
+    *rho_v = rv;
+    *rho_l = rl;
+    return LBM_OK;
+}
+
 }  // namespace lbm_host

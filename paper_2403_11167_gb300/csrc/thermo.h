@@ -22,5 +22,8 @@ int fe_theory(const CS& eos, double T, double rho_v, double rho_l, double p0, do
 // Continuum planar profile of the pseudopotential model (Eq. S44, S46).
 int pp_theory(const CS& eos, double T, double rho_v, double rho_l, double p0, double eps,
               double kappa_P, double kappa_Li, double* width, double* gamma);
+// Consistent densities of a 2-D droplet: equal chemical potential, p(rho_l) - p(rho_v) =
+// gamma / radius (Laplace), Newton from (rho_v, rho_l).
+int kelvin_2d(const CS& eos, double T, double gamma, double radius, double* rho_v, double* rho_l);
 
 }  // namespace lbm_host

@@ -14,13 +14,10 @@
   thermodynamically consistent vapour density of a droplet with that gamma (``kelvin_2d``).
   All droplets run as one batch.
 
-Everything here composes library calls (parameter resolution, batches, contexts,
-observables); the host-side Carnahan-Starling formulas below are only used to evaluate the
-consistent droplet densities.
+Everything here composes library calls (parameter resolution, the consistent droplet
+densities of lbm_kelvin_2d, batches, contexts, observables).
 """
 from __future__ import annotations
-
-import math
 
 import numpy as np
 
@@ -80,49 +77,19 @@ def table1(steps: int = 60000, nx: int = 100, fe_steps: int = 30000) -> dict:
     return out
 
 
-# ----------------------------------------------------------------------------------------
-# Carnahan-Starling pressure and chemical potential (Eqs. 28, 29) on the host, for the
-# consistent densities of a droplet.
-
-def _p_cs(rho, a, b, R, T):
-    e = b * rho / 4.0
-    return rho * R * T * (1 + e + e * e - e ** 3) / (1 - e) ** 3 - a * rho * rho
-
-
-def _mu_cs(rho, a, b, R, T):
-    e = b * rho / 4.0
-    return R * T * (3.0 - e) / (1.0 - e) ** 3 + R * T * math.log(rho) + R * T - 2.0 * a * rho
-
-
-def _dp(rho, a, b, R, T, h=1e-7):
-    return (_p_cs(rho + h, a, b, R, T) - _p_cs(rho - h, a, b, R, T)) / (2 * h)
-
-
 def kelvin_2d(a: float, b: float, R: float, T: float, gamma: float, radius: float, rho_v0: float,
               rho_l0: float) -> tuple[float, float]:
     """Thermodynamically consistent densities of a 2-D droplet of the given radius and surface
-    tension: equal chemical potential in both phases and p(rho_l) - p(rho_v) = gamma / radius
-    (Laplace), by Newton's method from the planar (Maxwell) pair (rho_v0, rho_l0)."""
-    rv, rl = rho_v0, rho_l0
-    for _ in range(50):
-        f1 = _mu_cs(rl, a, b, R, T) - _mu_cs(rv, a, b, R, T)
-        f2 = _p_cs(rl, a, b, R, T) - _p_cs(rv, a, b, R, T) - gamma / radius
-        # d mu / d rho = (dp/drho) / rho
-        j11, j12 = -_dp(rv, a, b, R, T) / rv, _dp(rl, a, b, R, T) / rl
-        j21, j22 = -_dp(rv, a, b, R, T), _dp(rl, a, b, R, T)
-        det = j11 * j22 - j12 * j21
-        drv = (-f1 * j22 + f2 * j12) / det
-        drl = (-j11 * f2 + j21 * f1) / det
-        rv, rl = rv + drv, rl + drl
-        if abs(drv) < 1e-15 * rv and abs(drl) < 1e-15 * rl:
-            break
-    return rv, rl
+    tension (lbm_kelvin_2d: equal chemical potential, Laplace jump gamma / radius), from the
+    planar (Maxwell) pair."""
+    return L.lbm_kelvin_2d(a, b, R, T, gamma, radius, rho_v0, rho_l0)
 
 
-def fig5(kappa_li_values=(-3.0, -2.4, -1.7, -1.2, -0.6, 0.0), steps: int = 20000) -> list:
+def fig5(kappa_li_values=(-3.0, -2.4, -1.7, -1.2, -0.6, 0.0), steps: int = 20000, fields: bool = False) -> list:
     """Per kappa^Li: surface tension gamma of the model (planar theory), the measured droplet
     vapour density, the consistent one (kelvin_2d at the measured equimolar radius), both
-    reduced by rho_c, and the relative error."""
+    reduced by rho_c, and the relative error; with ``fields`` also the droplet's final density
+    field (``rho``), its initial density (``rho0``) and its resolved parameters."""
     c = FIG5_COND
     specs, rhos, ths = [], [], []
     for kli in kappa_li_values:
@@ -137,10 +104,13 @@ def fig5(kappa_li_values=(-3.0, -2.4, -1.7, -1.2, -0.6, 0.0), steps: int = 20000
     b = L.Batch(specs, rhos)
     b.run()
     rows = []
-    for kli, th, o in zip(kappa_li_values, ths, b.observables()):
+    for i, (kli, th, o) in enumerate(zip(kappa_li_values, ths, b.observables())):
         rv_c, _ = kelvin_2d(c["a"], 4.0, 1.0, th.T, th.gamma, o["radius"], th.rho_v, th.rho_l)
         rows.append(dict(kappa_li=kli, gamma=th.gamma, radius=o["radius"], rho_v=o["rho_v"] / th.rho_c,
                          rho_v_consistent=rv_c / th.rho_c, rel_err=o["rho_v"] / rv_c - 1.0,
                          status=o["status"]))
+        if fields:
+            rows[-1].update(rho=b.populations(i).sum(0), rho0=rhos[i], params=_resolve(specs[i]["params"]),
+                            rho_v_abs=o["rho_v"], rho_c=th.rho_c)
     b.close()
     return rows

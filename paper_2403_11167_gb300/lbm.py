@@ -143,6 +143,7 @@ def _lib():
             "lbm_batch_last_error": ([], ctypes.c_char_p),
             "lbm_selftest_bounded_wait": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "lbm_resolve_params_many": ([ctypes.c_int, P, P, T, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "lbm_kelvin_2d": ([ctypes.c_double] * 6 + [dp, dp], ctypes.c_int),
             "lbm_surrogate_num_params": ([], ctypes.c_int),
             "lbm_surrogate_create": ([fp, ctypes.c_uint, ctypes.POINTER(vp)], ctypes.c_int),
             "lbm_surrogate_stats": ([vp, fp], ctypes.c_int),
@@ -401,6 +402,13 @@ def sweep_specs(entries, precision=LBM_F32):
         specs.append(dict(nx=e["nx"], ny=e["ny"], geometry=e["geometry"], nsteps=e["nsteps"], params=p))
         rhos.append(inputs.sweep_density(e, th.rho_v, th.rho_l))
     return specs, rhos
+
+
+def lbm_kelvin_2d(a, b, R, T, gamma, radius, rho_v0, rho_l0):
+    """Consistent (rho_v, rho_l) of a 2-D droplet (equal mu, Laplace jump gamma / radius)."""
+    rv, rl = ctypes.c_double(rho_v0), ctypes.c_double(rho_l0)
+    _check(_lib().lbm_kelvin_2d(a, b, R, T, gamma, radius, ctypes.byref(rv), ctypes.byref(rl)), "lbm_kelvin_2d")
+    return rv.value, rl.value
 
 
 def lbm_resolve_params_many(params_list):

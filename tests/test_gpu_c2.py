@@ -69,8 +69,9 @@ def test_static_droplets_fp32_against_oracle(model, Tr):
     assert all(o["status"] == lbm.LBM_OK for o in late)
     for R, o in zip(RADII, late):
         print(f"model {model} Tr {Tr} R {R} at 2e4: radius {o['radius']:.3f} dp {o['dp']:.4e} u_max {o['u_max']:.2e}")
-    # static: the equimolar radius moved by less than 2% from step 1e4 to 2e4
-    alive = [(R, o) for (R, *_, r1), o in zip(rows, late) if abs(o["radius"] / r1 - 1) < 0.02]
+    # static: the equimolar radius moved by less than 2% from step 1e4 to 2e4 (an evaporated
+    # droplet has no liquid probe left, and its radius reads 0 or garbage)
+    alive = [(R, o) for (R, *_, r1), o in zip(rows, late) if r1 > 0.5 * R and abs(o["radius"] / r1 - 1) < 0.02]
     gone = [R for (R, *_), o in zip(rows, late) if all(R != a for a, _ in alive)]
     assert len(alive) >= 3 and all(R <= 20 for R in gone), gone
     inv = np.array([1.0 / o["radius"] for _, o in alive])
