@@ -312,27 +312,32 @@ __device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__fadd2_rn(a.v, 
 __device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__ffma2_rn(a.v, b.v, make_float2(0.0f, 0.0f))); }
 __device__ __forceinline__ F2 fmav(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
 
-// Eq. (29) relative to the coexistence reference (see mu_bulk_rel), one cell, explicit ops.
-__device__ __forceinline__ float mu_bulk_f1(float rho, const StepParams<float>& P) {
-    const bool liq = rho >= P.rho_split;
-    const float rr = liq ? P.rho_ref_l : P.rho_ref_v;
-    const float ur = liq ? P.ur_l : P.ur_v;
-    const float ur3 = liq ? P.ur3_l : P.ur3_v;
-    const float irr = liq ? P.irr_l : P.irr_v;
-    const F1 d = F1(rho) - F1(rr);
-    const F1 u = fmav(F1(-P.b4), F1(rho), F1(1.0f));
-    const F1 U(ur);
-    const F1 num = fmav(F1(2.0f), fmav(U, U, fmav(U, u, u * u)), (U + u) * u * U);
-    const F1 dg = F1(P.b4) * d * num * F1(__frcp_rn((u * u * u * F1(ur3)).v));
-    const F1 lg(log1pf((d * F1(irr)).v));
-    return (fmav(F1(P.RT), dg + lg, F1(-2.0f * P.a) * d) + F1(liq ? P.mu_off_l : 0.0f)).v;
-}
-__device__ __forceinline__ F1 mu_bulk_v(F1 rho, const StepParams<float>& P) { return F1(mu_bulk_f1(rho.v, P)); }
-__device__ __forceinline__ F2 mu_bulk_v(F2 rho, const StepParams<float>& P) {
-    return F2(mu_bulk_f1(rho.v.x, P), mu_bulk_f1(rho.v.y, P));
-}
 __device__ __forceinline__ F1 rcp_v(F1 x) { return F1(__frcp_rn(x.v)); }
 __device__ __forceinline__ F2 rcp_v(F2 x) { return F2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
+__device__ __forceinline__ F1 log1p_v(F1 x) { return F1(log1pf(x.v)); }
+__device__ __forceinline__ F2 log1p_v(F2 x) { return F2(log1pf(x.v.x), log1pf(x.v.y)); }
+// per lane: l where rho >= split (liquid branch), v elsewhere
+__device__ __forceinline__ F1 pick_v(F1 rho, float split, float l, float v) { return F1(rho.v >= split ? l : v); }
+__device__ __forceinline__ F2 pick_v(F2 rho, float split, float l, float v) {
+    return F2(rho.v.x >= split ? l : v, rho.v.y >= split ? l : v);
+}
+
+// Eq. (29) relative to the coexistence reference (see mu_bulk_rel), explicit ops; the
+// reference (liquid or vapour branch), log1p and the reciprocal are taken per lane.
+template <class F>
+__device__ __forceinline__ F mu_bulk_v(F rho, const StepParams<float>& P) {
+    const F rr = pick_v(rho, P.rho_split, P.rho_ref_l, P.rho_ref_v);
+    const F U = pick_v(rho, P.rho_split, P.ur_l, P.ur_v);
+    const F ur3 = pick_v(rho, P.rho_split, P.ur3_l, P.ur3_v);
+    const F irr = pick_v(rho, P.rho_split, P.irr_l, P.irr_v);
+    const F off = pick_v(rho, P.rho_split, P.mu_off_l, 0.0f);
+    const F d = rho - rr;
+    const F u = fmav(F::c(-P.b4), rho, F::c(1.0f));
+    const F num = fmav(F::c(2.0f), fmav(U, U, fmav(U, u, u * u)), (U + u) * u * U);
+    const F dg = F::c(P.b4) * d * num * rcp_v(u * u * u * ur3);
+    const F lg = log1p_v(d * irr);
+    return fmav(F::c(P.RT), dg + lg, F::c(-2.0f * P.a) * d) + off;
+}
 
 template <class F>
 __device__ __forceinline__ F sum9_v(const F v[9]) {

@@ -44,32 +44,31 @@ __device__ __forceinline__ void pull_pair(const float* Rm, const float* R0, cons
     v[8] = F2(Rp[8 * W8 + sc - 1], Rp[8 * W8 + sc]);
 }
 
-// A row of a field held as pairs, with the left neighbour of the first cell (L) and the right
-// neighbour of the second (R) from the adjacent lanes.
+// A row of a field held as pairs (c: the lane's two cells) with its x-shifted pairs formed
+// once from the adjacent lanes: the values at x - 1 (xm) and x + 1 (xp) of both cells, so that
+// each use of the row reads them without re-pairing registers.
 struct Row2 {
-    F2 c;
-    float L, R;
+    F2 c, xm, xp;
 };
-__device__ __forceinline__ Row2 with_neighbours(F2 c) {
+__device__ __forceinline__ Row2 with_shifted(F2 c) {
     Row2 r;
     r.c = c;
-    r.L = __shfl_up_sync(0xffffffffu, c.v.y, 1);
-    r.R = __shfl_down_sync(0xffffffffu, c.v.x, 1);
+    r.xm = F2(__shfl_up_sync(0xffffffffu, c.v.y, 1), c.v.x);
+    r.xp = F2(c.v.y, __shfl_down_sync(0xffffffffu, c.v.x, 1));
     return r;
 }
-
 // Values at x + c_i (i = 1..8) of both cells of a lane, from the rows below (ym), at (y0) and
 // above (yp); y grows with the row index.
 __device__ __forceinline__ void neighbours_pair(const Row2& ym, const Row2& y0, const Row2& yp, F2 n[9]) {
     n[0] = y0.c;
-    n[1] = F2(y0.c.v.y, y0.R);   // (+1, 0)
-    n[2] = yp.c;                 // ( 0, +1)
-    n[3] = F2(y0.L, y0.c.v.x);   // (-1, 0)
-    n[4] = ym.c;                 // ( 0, -1)
-    n[5] = F2(yp.c.v.y, yp.R);   // (+1, +1)
-    n[6] = F2(yp.L, yp.c.v.x);   // (-1, +1)
-    n[7] = F2(ym.L, ym.c.v.x);   // (-1, -1)
-    n[8] = F2(ym.c.v.y, ym.R);   // (+1, -1)
+    n[1] = y0.xp;  // (+1, 0)
+    n[2] = yp.c;   // ( 0, +1)
+    n[3] = y0.xm;  // (-1, 0)
+    n[4] = ym.c;   // ( 0, -1)
+    n[5] = yp.xp;  // (+1, +1)
+    n[6] = yp.xm;  // (-1, +1)
+    n[7] = ym.xm;  // (-1, -1)
+    n[8] = ym.xp;  // (+1, -1)
 }
 
 template <int NW, int S>
@@ -128,7 +127,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
     const unsigned* qin = reinterpret_cast<const unsigned*>(rest_lo_plane(fin, P.pitch));
     unsigned* qout = reinterpret_cast<unsigned*>(rest_lo_plane(fout, P.pitch));
     r1.c = r2.c = r3.c = m2.c = m3.c = F2::c(1.0f);
-    r1.L = r1.R = r2.L = r2.R = r3.L = r3.R = m2.L = m2.R = m3.L = m3.R = 1.0f;
+    r1.xm = r1.xp = r2.xm = r2.xp = r3.xm = r3.xp = F2::c(1.0f);
+    m2.xm = m2.xp = m3.xm = m3.xp = F2::c(1.0f);
     bool ok = mbar_wait_bounded(&sm.full[0], 0) && mbar_wait_bounded(&sm.full[1], 0);
 #pragma unroll 1
     for (int q = y0 - 2; q <= y1 + 1 && ok; ++q) {
@@ -145,14 +145,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
             pull_pair<W8>(sm.stage[(k - 2) % S], sm.stage[(k - 1) % S], sm.stage[k % S], sc, v);
             rho0 = sum9_v(v);
         }
-        const Row2 r0 = with_neighbours(rho0);
+        const Row2 r0 = with_shifted(rho0);
         // mu(q-1) from rho rows q-2, q-1, q
         Row2 m1;
         {
             F2 rn[9];
             neighbours_pair(r2, r1, r0, rn);
             const F2 mu = (act && q >= y0) ? fe_mu_v(r1.c, rn, P) : F2::c(0.0f);
-            m1 = with_neighbours(mu);
+            m1 = with_shifted(mu);
         }
         // collide row q-2 (ring indices k-4 .. k-2 hold source rows q-3 .. q-1)
         if (out && q >= y0 + 2) {
@@ -233,7 +233,7 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
     const unsigned* qin = reinterpret_cast<const unsigned*>(rest_lo_plane(fin, P.pitch));
     unsigned* qout = reinterpret_cast<unsigned*>(rest_lo_plane(fout, P.pitch));
     p1.c = p2.c = F2::c(0.0f);
-    p1.L = p1.R = p2.L = p2.R = 0.0f;
+    p1.xm = p1.xp = p2.xm = p2.xp = F2::c(0.0f);
     F2 rho1 = F2::c(1.0f);  // rho of row q-1
     bool ok = mbar_wait_bounded(&sm.full[0], 0) && mbar_wait_bounded(&sm.full[1], 0);
 #pragma unroll 1
@@ -251,7 +251,7 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
             rho0 = sum9_v(v);
             psi = pseudo_psi_v(rho0, P);
         }
-        const Row2 p0 = with_neighbours(psi);
+        const Row2 p0 = with_shifted(psi);
         // collide row q-1 (ring indices k-3 .. k-1 hold source rows q-2 .. q)
         if (out && q > y0) {
             F2 v[9], pn[9];
