@@ -302,9 +302,10 @@ def run_walls(args, peak):
     the wall kernel; two launches per step) on a size x size plate channel (vapour below, liquid above, sine-perturbed
     interface, F_x = 1e-6), CUDA events around 500 steps on the launching stream; and the
     wall-clock rate of the 101 x 50 FP64 channel of Sec. 5.3 (steps/s over 2e4 steps); and the
-    droplet-collision drive of Sec. 5.4 (a domain-mean reduction plus a direct step per step):
-    steps/s of the 200 x 100 FP64 pair, and FP32 throughput of a size x size pair (the extra
-    read of the reduction is not counted in the algorithmic bytes of the fraction)."""
+    droplet-collision drive of Sec. 5.4: steps/s of the 200 x 100 FP64 pair (a domain-mean
+    reduction plus a direct step per step), and FP32 throughput of a size x size pair (the
+    driven strip kernels, rho_ave from the masses the previous step stored; one reduction per
+    64-step graph)."""
     import numpy as np
     import torch
 
@@ -351,7 +352,7 @@ def run_walls(args, peak):
             rates[key] = 20000 / (time.perf_counter() - t)
             ctx.close()
         out["sec53_channel_f64_steps_per_s"] = rates
-        # Sec. 5.4: droplet pair driven together (domain-mean reduction + direct step per step)
+        # Sec. 5.4: droplet pair driven together (FP64: reduction + direct step; FP32: driven strip kernels)
         col = {}
         for model, key in ((0, "pseudopotential"), (1, "free_energy")):
             kw = dict(a=0.25, Tr=0.8, tau_nu=1.0)

@@ -85,6 +85,7 @@ struct lbm_ctx {
     bool walls;          // no-slip walls on rows 0 and ny-1 (direct wall kernels)
     bool onesided;       // free-energy walls with the one-sided normal mu gradient (LBM_BC_WALL_ZOUHE_ONESIDED)
     void* wall;          // 14 nx reals: the wall rows' J_y and solve scratch (fe_wall_solve_kernel)
+    double* dmass;       // per-warp stored mass of the driven FP32 strip steps (drive_mass_slots)
     bool drive;          // droplet-collision drive configured (lbm_set_drive)
     bool grav;           // gravity configured (lbm_set_gravity; free-energy model)
     double g, rho_g, y_ref;
@@ -307,15 +308,22 @@ static size_t buffer_bytes(int precision, int nx, int ny) {
     return align256((precision == LBM_F64 ? 9 : 10) * (size_t)plane_pitch(nx, ny) * esz);
 }
 
+// Slots of the driven FP32 strip steps' per-warp stored mass: one per consumer warp of every
+// strip CTA (strip widths of at most 240 columns, strips of at least one row).
+static size_t drive_mass_slots(int nx, int ny) {
+    static_assert(kPPPTX == kFEPTX && kPPPWarps == kFEPWarps, "both strip kernels share one slot layout");
+    return (size_t)((nx + kPPPTX - 1) / kPPPTX) * (size_t)ny * kPPPWarps;
+}
+
 extern "C" size_t lbm_workspace_bytes(int precision, int nx, int ny) {
     if (nx < 1 || ny < 1) return 0;
     const size_t esz = precision == LBM_F64 ? 8 : 4;
     const size_t n = (size_t)nx * ny;
     const size_t fbytes = buffer_bytes(precision, nx, ny);
     const size_t fields = align256(4 * n * esz);
-    // ... + the one-sided walls' row solve (14 nx reals)
+    // ... + the one-sided walls' row solve (14 nx reals) + the drive's mass slots
     return 2 * fbytes + fields + align256(kRedBlocks * 3 * sizeof(double)) + align256(8 * sizeof(double)) + 256 +
-           align256(14 * (size_t)nx * esz);
+           align256(14 * (size_t)nx * esz) + align256(drive_mass_slots(nx, ny) * sizeof(double));
 }
 
 template <typename real>
@@ -438,6 +446,7 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
     c->d_obs = reinterpret_cast<double*>(reinterpret_cast<char*>(c->partials) + align256(kRedBlocks * 3 * sizeof(double)));
     c->d_err = reinterpret_cast<int*>(reinterpret_cast<char*>(c->d_obs) + align256(8 * sizeof(double)));
     c->wall = reinterpret_cast<char*>(c->d_err) + 256;
+    c->dmass = reinterpret_cast<double*>(static_cast<char*>(c->wall) + align256(14 * (size_t)nx * c->esz));
     c->walls = walls;
     c->onesided = bc_y == LBM_BC_WALL_ZOUHE_ONESIDED && p->model == LBM_FREE_ENERGY;
     // walls: the periodic strip kernels serve the interior when both wall bands fit
@@ -478,6 +487,12 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FEPSmem));
         cudaError_t e2 = cudaFuncSetAttribute(lbmk::pp_step_pair<kPPPWarps, kPPPStages>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPPSmem));
+        if (e1 == cudaSuccess)  // the driven instantiations (Sec. 5.4 drive)
+            e1 = cudaFuncSetAttribute(lbmk::fe_step_pair<kFEPWarps, kFEPStages, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FEPSmem));
+        if (e2 == cudaSuccess)
+            e2 = cudaFuncSetAttribute(lbmk::pp_step_pair<kPPPWarps, kPPPStages, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPPSmem));
         if (e1 != cudaSuccess || e2 != cudaSuccess) {
             lbm_destroy(c);
             return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaFuncSetAttribute(max dynamic smem)");
@@ -546,12 +561,41 @@ constexpr int kWallIters = 32;
 template <typename real>
 static const real* launch_wall_solve(lbm_ctx* c, int src, const lbmk::StepParams<real>& sp);
 
-// One step with the droplet-collision drive acting (periodic lattice, direct kernels).
-static int launch_step_driven(lbm_ctx* c, int src) {
+// The drive of a state whose mass the previous driven strip step left in c->dmass (its
+// per-warp sums of the populations it stored): rho_ave = their fixed-order sum / cells.
+static lbmk::Drive<float> chained_drive(lbm_ctx* c, dim3 grid) {
+    const long long n = (long long)c->nx * c->ny;
+    lbmk::mass_final_kernel<<<1, 32, 0, c->stream>>>(c->dmass, (int)(grid.x * grid.y) * kPPPWarps, 1.0 / (double)n,
+                                                     c->partials + kMassBlocks);
+    lbmk::Drive<float> d;
+    d.rho_ave = c->partials + kMassBlocks;
+    d.x_split = (int)std::floor(std::min(std::max(c->drive_split, -1.0), (double)c->nx));
+    d.ax_lo = (float)c->drive_lo;
+    d.ax_hi = (float)c->drive_hi;
+    return d;
+}
+
+// One step with the droplet-collision drive acting (periodic lattice).  FP32 lattices that
+// run the strip kernels run their DRIVE instantiation: rho_ave of the state comes from the
+// masses the previous driven step stored (chained: the step before, in the same graph) or,
+// for the first step of a sequence, from the block-sum reduction; FP64 and other shapes run
+// the direct kernels after the reduction.
+static int launch_step_driven(lbm_ctx* c, int src, bool chained) {
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
-    if (c->prec == LBM_F32) {
+    if (c->prec == LBM_F32 && c->use_tma) {
+        dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
+        const lbmk::Drive<float> d = chained ? chained_drive(c, grid) : launch_drive<float>(c, src);
+        if (pp)
+            lbmk::pp_step_pair<kPPPWarps, kPPPStages, true>
+                <<<grid, (kPPPWarps + 1) * 32, sizeof(PPPSmem), c->stream>>>((const float*)fin, (float*)fout, c->spf,
+                                                                             c->d_err, d, c->dmass);
+        else
+            lbmk::fe_step_pair<kFEPWarps, kFEPStages, true>
+                <<<grid, (kFEPWarps + 1) * 32, sizeof(FEPSmem), c->stream>>>((const float*)fin, (float*)fout, c->spf,
+                                                                             c->d_err, d, c->dmass);
+    } else if (c->prec == LBM_F32) {
         const lbmk::Drive<float> d = launch_drive<float>(c, src);
         dim3 grid((c->nx + kTXf - 1) / kTXf, (c->ny + c->rows - 1) / c->rows);
         if (pp)
@@ -614,7 +658,9 @@ static const real* launch_wall_solve(lbm_ctx* c, int src, const lbmk::StepParams
     return w;
 }
 
-static int launch_step(lbm_ctx* c, int src, bool driven = false) {
+// chained: the previous launch on the stream was a driven step of the same sequence (a graph
+// replays its steps in order), so a driven strip step may take rho_ave from its stored masses.
+static int launch_step(lbm_ctx* c, int src, bool driven = false, bool chained = false) {
     if (uses_iwb(c)) {
         if (c->prec == LBM_F32)
             launch_iwb<float, kTXf>(c, src, driven, c->spf);
@@ -623,7 +669,7 @@ static int launch_step(lbm_ctx* c, int src, bool driven = false) {
         CK(cudaGetLastError());
         return LBM_OK;
     }
-    if (driven) return launch_step_driven(c, src);
+    if (driven) return launch_step_driven(c, src, chained);
     const void* fin = c->f[src];
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
@@ -694,7 +740,7 @@ static int build_graph(lbm_ctx* c, int parity, int driven) {
     int rc = LBM_OK;
     int src = parity;
     for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) {
-        rc = launch_step(c, src, driven != 0);
+        rc = launch_step(c, src, driven != 0, k > 0);
         src ^= 1;
     }
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);

@@ -430,15 +430,16 @@ __device__ __forceinline__ void apply_dm_v(F v[9], F de, F dz, F djx, F dqx, F d
 
 // Improved well-balanced free-energy collision (Eqs. 1, 6, 20, 21, 24); mn, rn: mu and rho
 // at x + c_i (i = 1..8).  COMP: the rest population's increment goes to *d0, v[0] unchanged.
+// fx: the x body force of the cell (P.fx, or P.fx plus the droplet-collision drive).
 template <class F, bool COMP = false>
-__device__ __forceinline__ void fe_collide_v(F v[9], F rho, const F mn[9], const F rn[9],
-                                             const StepParams<float>& P, F* d0 = nullptr) {
+__device__ __forceinline__ void fe_collide_fx_v(F v[9], F rho, const F mn[9], const F rn[9], F fx,
+                                                const StepParams<float>& P, F* d0) {
     const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
     const F gmx = fmav(mn[1] - mn[3], w1, ((mn[5] - mn[7]) + (mn[8] - mn[6])) * w2);
     const F gmy = fmav(mn[2] - mn[4], w1, ((mn[5] - mn[7]) + (mn[6] - mn[8])) * w2);
     const F grx = fmav(rn[1] - rn[3], w1, ((rn[5] - rn[7]) + (rn[8] - rn[6])) * w2);
     const F gry = fmav(rn[2] - rn[4], w1, ((rn[5] - rn[7]) + (rn[6] - rn[8])) * w2);
-    const F Fx = fmav(-rho, gmx, F::c(P.fx)), Fy = fmav(-rho, gmy, F::c(P.fy));
+    const F Fx = fmav(-rho, gmx, fx), Fy = fmav(-rho, gmy, F::c(P.fy));
     const F jx = mom_jx(v);
     const F jy = mom_jy(v);
     const F inv_rho = rcp_v(rho);
@@ -469,6 +470,11 @@ __device__ __forceinline__ void fe_collide_v(F v[9], F rho, const F mn[9], const
     const F dpxy = fmav(F::c(hn), fmav(ux, Gy, uy * Gx), F::c(-P.s_nu) * (pxy - rho * ux * uy));
     apply_dm_v<F, COMP>(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy, d0);
 }
+template <class F, bool COMP = false>
+__device__ __forceinline__ void fe_collide_v(F v[9], F rho, const F mn[9], const F rn[9],
+                                             const StepParams<float>& P, F* d0 = nullptr) {
+    fe_collide_fx_v<F, COMP>(v, rho, mn, rn, F::c(P.fx), P, d0);
+}
 
 // Carnahan-Starling pressure (Eq. 28) and pseudopotential (Eq. 11, G = -1), explicit ops.
 template <class F>
@@ -490,13 +496,14 @@ __device__ __forceinline__ F pseudo_psi_v(F rho, const StepParams<float>& P) {
 // pc = psi at the cell, pn[i] = psi at x + c_i (i = 1..8).
 // COMP: compensated rest population with the moving populations' rounding absorbed (the rest
 // increment goes to *d0, v[0] unchanged; see apply_dm_v and rest_update).
+// fx: the x body force of the cell (P.fx, or P.fx plus the droplet-collision drive).
 template <class F, bool COMP = false>
-__device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9], const StepParams<float>& P,
-                                             F* d0 = nullptr) {
+__device__ __forceinline__ void pp_collide_fx_v(F v[9], F rho, F pc, const F pn[9], F fx,
+                                                const StepParams<float>& P, F* d0) {
     const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
     const F Sx = div12(stencil12_x(pn));
     const F Sy = div12(stencil12_y(pn));
-    const F Fx = fmav(pc, Sx, F::c(P.fx)), Fy = fmav(pc, Sy, F::c(P.fy));
+    const F Fx = fmav(pc, Sx, fx), Fy = fmav(pc, Sy, F::c(P.fy));
     const F d1 = pn[1] - pc, d2 = pn[2] - pc, d3 = pn[3] - pc, d4 = pn[4] - pc;
     const F d5 = pn[5] - pc, d6 = pn[6] - pc, d7 = pn[7] - pc, d8 = pn[8] - pc;
     const F dd = ((d5 + d6) + (d7 + d8)) * w2;
@@ -536,6 +543,21 @@ __device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9],
     // j* - j = F exactly (tau_j drops out)
     apply_dm_v<F, COMP, COMP>(v, de, dz, Fx, dqx, Fy, dqy, dpxx, dpxy, d0);
 }
+template <class F, bool COMP = false>
+__device__ __forceinline__ void pp_collide_v(F v[9], F rho, F pc, const F pn[9], const StepParams<float>& P,
+                                             F* d0 = nullptr) {
+    pp_collide_fx_v<F, COMP>(v, rho, pc, pn, F::c(P.fx), P, d0);
+}
+
+// Droplet-collision drive (Sec. 5.4): the force a_x |rho - rho_ave| along x, a_x = ax_lo for
+// x <= x_split and ax_hi beyond, rho_ave the mean density of the state being collided (a device
+// scalar).  rho_ave == nullptr: no drive.
+template <typename real>
+struct Drive {
+    const double* rho_ave;
+    int x_split;
+    real ax_lo, ax_hi;
+};
 
 // ---------------------------------------------------------------------------------
 // Compensated rest population of the FP32 step (both models).

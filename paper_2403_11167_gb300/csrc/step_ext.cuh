@@ -129,14 +129,6 @@ __device__ __forceinline__ real wall_grad_y_onesided(const real n[9], bool top) 
     return -real(3) * (a * (n[4] - n[0]) + d * ((n[8] - n[1]) + (n[7] - n[3])));
 }
 
-// Droplet-collision drive; rho_ave == nullptr: none.
-template <typename real>
-struct Drive {
-    const double* rho_ave;  // mean density of the state being collided (device scalar)
-    int x_split;
-    real ax_lo, ax_hi;
-};
-
 // Full improved well-balanced free-energy terms (Eqs. 20, 21): the viscosity-tuning A and
 // gravity g along -y with reference density rho_g, p_g = rho_g g (y - y_ref).  on == 0: none.
 template <typename real>

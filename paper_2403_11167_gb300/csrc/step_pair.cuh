@@ -71,10 +71,36 @@ __device__ __forceinline__ void neighbours_pair(const Row2& ym, const Row2& y0, 
     n[8] = ym.xp;  // (+1, -1)
 }
 
-template <int NW, int S>
+// DRIVE: the droplet-collision drive of Sec. 5.4 adds a_x |rho - rho_ave| to each cell's x
+// force (rho_ave from D.rho_ave), and every consumer warp writes the sum of the populations it
+// stored -- the mass of the next state, which on a periodic lattice holds each stored population
+// once -- to mass[((blockIdx.y * gridDim.x) + blockIdx.x) * NW + warp] (0 for idle warps), so
+// that the next step's rho_ave needs no pass over the lattice.
+template <int NW, bool DRIVE>
+__device__ __forceinline__ void zero_mass_slots(double* mass) {
+    if (DRIVE && threadIdx.x < NW) mass[(blockIdx.y * gridDim.x + blockIdx.x) * NW + threadIdx.x] = 0.0;
+}
+// The two cells' x force with the drive: P.fx + a_x |rho - rho_ave| (ax: a_x of both cells).
+__device__ __forceinline__ F2 driven_fx(F2 rho, float rave, F2 ax, const StepParams<float>& P) {
+    const F2 dr = rho - F2::c(rave);
+    return fmav(ax, F2(fabsf(dr.v.x), fabsf(dr.v.y)), F2::c(P.fx));
+}
+// a_x of the cells at columns gx and gx + 1
+__device__ __forceinline__ F2 drive_ax(const Drive<float>& D, int gx) {
+    return F2(gx <= D.x_split ? D.ax_lo : D.ax_hi, gx + 1 <= D.x_split ? D.ax_lo : D.ax_hi);
+}
+// One warp's stored mass (two FP32 partial sums per lane) into its slot, fixed order.
+__device__ __forceinline__ void store_warp_mass(F2 macc, double* slot) {
+    double s = (double)macc.v.x + (double)macc.v.y;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) *slot = s;
+}
+
+template <int NW, int S, bool DRIVE = false>
 __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __restrict__ fin,
                                                                  float* __restrict__ fout, const StepParams<float> P,
-                                                                 int* __restrict__ err) {
+                                                                 int* __restrict__ err, const Drive<float> D = {},
+                                                                 double* __restrict__ mass = nullptr) {
     constexpr int TXW = 60;
     using Smem = WarpStripSmem<NW, S, TXW>;
     constexpr int W8 = Smem::W8;
@@ -84,7 +110,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
     const int wb = warp_strip_width(nx, gridDim.x);
     const int x0 = blockIdx.x * wb;
     const int w = min(wb, nx - x0);
-    if (w <= 0) return;
+    if (w <= 0) {
+        zero_mass_slots<NW, DRIVE>(mass);
+        return;
+    }
     const int y0 = blockIdx.y * P.rows;
     const int y1 = min(y0 + P.rows, P.ny);
     const int rbase = y0 - 3;
@@ -111,7 +140,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
         }
         return;
     }
-    if (warp >= nwa) return;
+    double* const mslot = DRIVE ? mass + (blockIdx.y * gridDim.x + blockIdx.x) * NW + warp : nullptr;
+    if (warp >= nwa) {
+        if (DRIVE && lane == 0) *mslot = 0.0;
+        return;
+    }
     // consumer warp: columns [cw, cw + nw) of the strip (nw even, > 0), lane l at columns
     // cw - 2 + 2l and cw - 1 + 2l
     const int cw = warp * 60;
@@ -129,6 +162,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
     r1.c = r2.c = r3.c = m2.c = m3.c = F2::c(1.0f);
     r1.xm = r1.xp = r2.xm = r2.xp = r3.xm = r3.xp = F2::c(1.0f);
     m2.xm = m2.xp = m3.xm = m3.xp = F2::c(1.0f);
+    const float rave = DRIVE ? (float)*D.rho_ave : 0.0f;
+    const F2 ax = DRIVE ? drive_ax(D, x0 + col) : F2::c(0.0f);
+    F2 macc = F2::c(0.0f);
     bool ok = mbar_wait_bounded(&sm.full[0], 0) && mbar_wait_bounded(&sm.full[1], 0);
 #pragma unroll 1
     for (int q = y0 - 2; q <= y1 + 1 && ok; ++q) {
@@ -161,10 +197,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
             neighbours_pair(m3, m2, m1, mn);
             neighbours_pair(r3, r2, r1, rn);
             F2 d0;
-            fe_collide_v<F2, true>(v, r2.c, mn, rn, P, &d0);
+            if constexpr (DRIVE)
+                fe_collide_fx_v<F2, true>(v, r2.c, mn, rn, driven_fx(r2.c, rave, ax, P), P, &d0);
+            else
+                fe_collide_v<F2, true>(v, r2.c, mn, rn, P, &d0);
             cp_async_wait<2>();  // the copy of row q-2's extensions (two groups ago) has landed
             const unsigned ql2 = sm.qext[(q - 2 - y0 + 3) % 3][warp][lane];
             const unsigned qw = rest_update_pair(v[0], ql2, d0, P);  // compensated rest population
+            if constexpr (DRIVE) macc = macc + sum9_v(v);
             const long long oc = (long long)(q - 2) * nx + x0 + col;
             float* o = fout + oc;
 #pragma unroll
@@ -181,6 +221,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
         m2 = m1;
     }
     cp_async_wait<0>();
+    if constexpr (DRIVE) store_warp_mass(macc, mslot);
     if (!ok) atomicExch(err, 1);
 }
 
@@ -190,10 +231,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_step_pair(const float* __
 // row q-2.  Lanes 0 and nw/2 + 1 supply the psi halo columns.
 // One CTA's strip of the pseudopotential step: columns [x0, x0 + w) (w <= 60 NW, x0 and w
 // multiples of 4), rows [y0, y1).  Called by every thread of the CTA.
-template <int NW, int S>
+// DRIVE: as for fe_step_pair; mass points to this CTA's NW slots.
+template <int NW, int S, bool DRIVE = false>
 __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, float* __restrict__ fout,
                                               const StepParams<float>& P, int x0, int w, int y0, int y1,
-                                              WarpStripSmem<NW, S, 60>& sm, int* __restrict__ err) {
+                                              WarpStripSmem<NW, S, 60>& sm, int* __restrict__ err,
+                                              const Drive<float>* D = nullptr, double* mass = nullptr) {
     constexpr int W8 = WarpStripSmem<NW, S, 60>::W8;
     const int nx = P.nx;
     const int rbase = y0 - 2;
@@ -220,7 +263,10 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
         }
         return;
     }
-    if (warp >= nwa) return;
+    if (warp >= nwa) {
+        if (DRIVE && lane == 0) mass[warp] = 0.0;
+        return;
+    }
     const int cw = warp * 60;
     const int nw = min(60, w - cw);
     const int col = cw - 2 + 2 * lane;
@@ -235,6 +281,9 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
     p1.c = p2.c = F2::c(0.0f);
     p1.xm = p1.xp = p2.xm = p2.xp = F2::c(0.0f);
     F2 rho1 = F2::c(1.0f);  // rho of row q-1
+    const float rave = DRIVE ? (float)*D->rho_ave : 0.0f;
+    const F2 ax = DRIVE ? drive_ax(*D, x0 + col) : F2::c(0.0f);
+    F2 macc = F2::c(0.0f);
     bool ok = mbar_wait_bounded(&sm.full[0], 0) && mbar_wait_bounded(&sm.full[1], 0);
 #pragma unroll 1
     for (int q = y0 - 1; q <= y1 && ok; ++q) {
@@ -258,10 +307,14 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
             pull_pair<W8>(sm.stage[(k - 3) % S], sm.stage[(k - 2) % S], sm.stage[(k - 1) % S], sc, v);
             neighbours_pair(p2, p1, p0, pn);
             F2 d0;
-            pp_collide_v<F2, true>(v, rho1, pn[0], pn, P, &d0);
+            if constexpr (DRIVE)
+                pp_collide_fx_v<F2, true>(v, rho1, pn[0], pn, driven_fx(rho1, rave, ax, P), P, &d0);
+            else
+                pp_collide_v<F2, true>(v, rho1, pn[0], pn, P, &d0);
             cp_async_wait<1>();  // the copy of row q-1's extensions (one group ago) has landed
             const unsigned ql1 = sm.qext[(q - 1 - y0 + 3) % 3][warp][lane];
             const unsigned qw = rest_update_pair(v[0], ql1, d0, P);  // compensated rest population
+            if constexpr (DRIVE) macc = macc + sum9_v(v);
             const long long oc = (long long)(q - 1) * nx + x0 + col;
             float* o = fout + oc;
 #pragma unroll
@@ -276,22 +329,28 @@ __device__ __forceinline__ void pp_pair_strip(const float* __restrict__ fin, flo
         rho1 = rho0;
     }
     cp_async_wait<0>();
+    if constexpr (DRIVE) store_warp_mass(macc, mass + warp);
     if (!ok) atomicExch(err, 1);
 }
 
-template <int NW, int S>
+template <int NW, int S, bool DRIVE = false>
 __global__ void __launch_bounds__((NW + 1) * 32, 1) pp_step_pair(const float* __restrict__ fin,
                                                                  float* __restrict__ fout, const StepParams<float> P,
-                                                                 int* __restrict__ err) {
+                                                                 int* __restrict__ err, const Drive<float> D = {},
+                                                                 double* __restrict__ mass = nullptr) {
     using Smem = WarpStripSmem<NW, S, 60>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int wb = warp_strip_width(P.nx, gridDim.x);
     const int x0 = blockIdx.x * wb;
     const int w = min(wb, P.nx - x0);
-    if (w <= 0) return;
+    if (w <= 0) {
+        zero_mass_slots<NW, DRIVE>(mass);
+        return;
+    }
     const int y0 = blockIdx.y * P.rows;
-    pp_pair_strip<NW, S>(fin, fout, P, x0, w, y0, min(y0 + P.rows, P.ny), sm, err);
+    pp_pair_strip<NW, S, DRIVE>(fin, fout, P, x0, w, y0, min(y0 + P.rows, P.ny), sm, err, &D,
+                                DRIVE ? mass + (blockIdx.y * gridDim.x + blockIdx.x) * NW : nullptr);
 }
 
 }  // namespace lbmk
