@@ -392,7 +392,7 @@ def run_walls(args, peak):
         e1.record(stream)
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) * 1e-3 / 256
-        out["free_energy_A_f32"] = {"kernel": "fe_step_iwb", "mlups": size * size / sec / 1e6,
+        out["free_energy_A_f32"] = {"kernel": "fe_iwb_pair", "mlups": size * size / sec / 1e6,
                                     "frac_of_hbm": BYTES_PER_CELL[1] * size * size / sec / 1e9 / peak}
         ctx.close()
     return out

@@ -18,6 +18,7 @@
 #include "ring.cuh"
 #include "step_pair.cuh"
 #include "step_ext.cuh"
+#include "step_iwb_pair.cuh"
 #include "rest_host.h"
 #include "thermo.h"
 
@@ -61,6 +62,12 @@ constexpr int kFEPWarps = 4;                   // consumer warps per CTA
 constexpr int kFEPStages = LBM_FEP_STAGES;
 static_assert(kFEPStages >= 5, "the free-energy strip ring needs at least 5 stages");
 using FEPSmem = lbmk::WarpStripSmem<kFEPWarps, kFEPStages, 60>;
+// Strip kernel of the full free-energy model (A != 0, buoyancy): rows q-4 .. q+1 live, 8
+// stages; 154 registers a thread allow 2 CTAs per SM (capped at 3 CTAs it spilled and ran
+// 20% slower).
+constexpr int kIWBWarps = 4;
+constexpr int kIWBStages = 8;
+using IWBSmem = lbmk::IwbStripSmem<kIWBWarps, kIWBStages>;
 constexpr int kFEPTX = FEPSmem::TX;            // widest strip (240 columns)
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
@@ -493,6 +500,9 @@ extern "C" int lbm_create(const lbm_params* p, int nx, int ny, int bc_x, int bc_
         if (e2 == cudaSuccess)
             e2 = cudaFuncSetAttribute(lbmk::pp_step_pair<kPPPWarps, kPPPStages, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PPPSmem));
+        if (e1 == cudaSuccess)  // the full free-energy model's strip kernel
+            e1 = cudaFuncSetAttribute(lbmk::fe_iwb_pair<kIWBWarps, kIWBStages>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(IWBSmem));
         if (e1 != cudaSuccess || e2 != cudaSuccess) {
             lbm_destroy(c);
             return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaFuncSetAttribute(max dynamic smem)");
@@ -636,6 +646,17 @@ static lbmk::Ext<real> ext_terms(const lbm_ctx* c) {
 
 template <typename real, int TX>
 static void launch_iwb(lbm_ctx* c, int src, bool driven, const lbmk::StepParams<real>& sp) {
+    if constexpr (std::is_same<real, float>::value) {
+        // FP32 periodic lattices without the drive and with gravity's reference density 0 run the
+        // strip kernel; the rest the direct kernel
+        if (c->use_tma && !c->walls && !driven && (!c->grav || c->rho_g == 0.0)) {
+            dim3 grid((c->nx + IWBSmem::TX - 1) / IWBSmem::TX, (c->ny + c->rows - 1) / c->rows);
+            lbmk::fe_iwb_pair<kIWBWarps, kIWBStages><<<grid, (kIWBWarps + 1) * 32, sizeof(IWBSmem), c->stream>>>(
+                static_cast<const float*>(c->f[src]), static_cast<float*>(c->f[src ^ 1]), sp, ext_terms<float>(c),
+                c->d_err);
+            return;
+        }
+    }
     const lbmk::Drive<real> d = driven ? launch_drive<real>(c, src) : no_drive<real>();
     dim3 grid((c->nx + TX - 1) / TX, (c->ny + c->rows - 1) / c->rows);
     const real* fin = static_cast<const real*>(c->f[src]);

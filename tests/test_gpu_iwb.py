@@ -111,6 +111,73 @@ def test_fp32_A_droplet():
     assert err < 1e-5
 
 
+@pytest.mark.parametrize("shape,g", [((128, 96), 0.0), ((456, 120), 0.0), ((300, 64), 2e-6)])
+def test_fp32_A_strip_kernel_against_oracle(shape, g):
+    """FP32 full free-energy model in the strip kernel (nx % 4 == 0, periodic): A = 0.15,
+    droplet of radius ny/4, 100 steps, densities within 1e-5 of the oracle.
+    - Shapes: one strip of 128 columns; three strips of 152 (runs 56, 56, 40); and two strips
+      of 152 and 148 (the last run 36).
+    - g != 0 adds the buoyancy -rho g (gravity with reference density 0)."""
+    nx, ny = shape
+    ctx, rp, th = gpu_context(FE, F32, nx, ny, a=0.25, Tr=0.8, tau_nu=1.0, tau_e=0.9, A=0.15)
+    if g:
+        ctx.set_gravity(g, 0.0)
+    rho0 = inputs.droplet(nx, ny, ny / 4, th.rho_v, th.rho_l)
+    ctx.set_density(rho0)
+    ctx.step(100)
+    p = oracle_params(rp, th)
+    p.g, p.rho_g, p.y_ref = g, 0.0, 0.0
+    f_ref = O.run(FE, p, O.init_iwb(p, rho0), 100)
+    f = ctx.populations()
+    err = rho_err(f.sum(0), f_ref.sum(0))
+    print("fp32 A strip", shape, g, err, pop_err(f, f_ref))
+    assert err < 1e-5
+    assert pop_err(f, f_ref) < 1e-5
+    ctx.close()
+
+
+def test_fp32_A_strip_kernel_matches_direct_kernel(monkeypatch):
+    """The strip kernel and the direct kernel (fe_step_iwb) write the same equations with
+    different FP32 arithmetic: after 200 steps of an A = 0.15 droplet they agree to rounding."""
+    nx, ny = 256, 128
+    kw = dict(a=0.25, Tr=0.8, tau_nu=1.0, tau_e=0.9, A=0.15)
+    a, rp, th = gpu_context(FE, F32, nx, ny, **kw)
+    monkeypatch.setenv("LBM_NO_TMA", "1")
+    b, _, _ = gpu_context(FE, F32, nx, ny, **kw)
+    rho0 = inputs.droplet(nx, ny, 40.0, th.rho_v, th.rho_l)
+    for ctx in (a, b):
+        ctx.set_density(rho0)
+        ctx.step(200)
+    fa, fb = a.populations(), b.populations()
+    print("fp32 A strip vs direct", pop_err(fa, fb))
+    assert pop_err(fa, fb) < 5e-6  # measured 1.9e-6
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("A,tau", [(0.2, 1.0), (-0.2, 0.9)])
+def test_shear_wave_viscosity_fp32_strip_kernel(A, tau):
+    """FP32 shear wave through the strip kernel (L = 64, nx = 8): decay rate nu k^2 with
+    nu = c_s^2 (tau - 1/2 - A), within 0.5%."""
+    L, nx, U = 64, 8, 1e-3
+    ctx, rp, th = gpu_context(FE, F32, nx, L, a=0.25, Tr=0.8, tau_nu=tau, tau_e=1.0, A=A)
+    rho = th.rho_l
+    f = O.init(FE, np.full((L, nx), rho))
+    y = np.arange(L)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    f = f + (w * cx)[:, None, None] * 3.0 * rho * (U * np.sin(2 * np.pi * y / L))[None, :, None]
+    ctx.set_populations(f)
+    amps = []
+    for s in (200, 1000):
+        ctx.step(s)
+        _, ux, _ = ctx.fields()
+        amps.append(2.0 / L * np.sum(ux[:, 0] * np.sin(2 * np.pi * y / L)))
+    nu = -np.log(amps[1] / amps[0]) / ((2 * np.pi / L) ** 2 * 1000)
+    assert abs(nu / ((tau - 0.5 - A) / 3.0) - 1) < 5e-3, nu
+    ctx.close()
+
+
 @pytest.mark.parametrize("A,tau", [(0.2, 1.0), (-0.2, 0.9)])
 def test_shear_wave_viscosity_gpu(A, tau):
     """FP64 shear wave (L = 64): decay rate nu k^2 with nu = c_s^2 (tau - 1/2 - A), within 0.5%."""
