@@ -148,7 +148,10 @@ int lbm_kelvin_2d(double a, double b, double R, double T, double gamma, double r
  * n < 0 or NULL arrays with n > 0, else LBM_OK. */
 int lbm_resolve_params_many(int n, const lbm_params* in, lbm_params* out, lbm_thermo* th, int* status);
 
-/* Bytes of device workspace a context of this size and precision needs. */
+/* Bytes of device workspace a context of this size and precision needs: two population
+ * buffers (nine planes, plus the rest-population extension plane for FP32), four fields for
+ * the observables, reduction partials, the one-sided walls' row solve (14 nx reals) and one
+ * double per strip warp for the droplet-collision drive's stored mass (Sec. 5.4). */
 size_t lbm_workspace_bytes(int precision, int nx, int ny);
 
 /* Create a context for an nx x ny lattice (nx, ny >= 1).  Boundaries: bc_x must be
@@ -200,11 +203,14 @@ int lbm_set_gravity(lbm_ctx* ctx, double g, double rho_ref, double y_ref);
 /* Droplet-collision drive of Sec. 5.4: from now on the collision of every state at time
  * t > t_on (t = steps taken since lbm_set_density) adds to the x force of each cell
  *   F_x += a_x |rho - rho_ave|,  a_x = ax_lo where x <= x_split, ax_hi where x > x_split,
- * rho_ave the mean density of that state (reduced on the device every step).  The force is
- * external: it enters the total force (velocity, forcing moments) but not the interaction
- * force of the sigma^Li term (Eq. 32).  Sec. 5.4 uses ax_lo = 5e-6, ax_hi = -5e-6,
- * x_split = 100, t_on = 2000 on a 200 x 100 lattice.  Steps with the drive run the direct
- * kernels.  Errors: LBM_ERR_ARG for a non-finite value, LBM_ERR_UNSUPPORTED with walls (the
+ * rho_ave the mean density of that state.  The force is external: it enters the total force
+ * (velocity, forcing moments) but not the interaction force of the sigma^Li term (Eq. 32).
+ * Sec. 5.4 uses ax_lo = 5e-6, ax_hi = -5e-6, x_split = 100, t_on = 2000 on a 200 x 100 lattice.
+ * FP32 lattices on the strip kernels run their driven instantiation: each step also sums the
+ * populations it stores, which is the next state's mass, and the block-sum reduction runs
+ * only at the first step of each captured 64-step graph and at single steps.  FP64 and other
+ * shapes reduce every step and run the direct kernels.  The two differ only in the summation
+ * order of rho_ave.  Errors: LBM_ERR_ARG for a non-finite value, LBM_ERR_UNSUPPORTED with walls (the
  * reduction sums the stored populations of a periodic lattice).  Synchronises the stream. */
 int lbm_set_drive(lbm_ctx* ctx, double ax_lo, double ax_hi, double x_split, long long t_on);
 
