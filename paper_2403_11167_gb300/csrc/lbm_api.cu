@@ -63,8 +63,8 @@ constexpr int kFEPStages = LBM_FEP_STAGES;
 static_assert(kFEPStages >= 5, "the free-energy strip ring needs at least 5 stages");
 using FEPSmem = lbmk::WarpStripSmem<kFEPWarps, kFEPStages, 60>;
 // Strip kernel of the full free-energy model (A != 0, buoyancy): rows q-4 .. q+1 live, 8
-// stages; 154 registers a thread allow 2 CTAs per SM (capped at 3 CTAs it spilled and ran
-// 20% slower).
+// stages, 3 CTAs per SM (128 registers without spills, the velocity derivatives being taken
+// before the collision's populations are pulled).
 constexpr int kIWBWarps = 4;
 constexpr int kIWBStages = 8;
 using IWBSmem = lbmk::IwbStripSmem<kIWBWarps, kIWBStages>;

@@ -48,9 +48,27 @@ __device__ __forceinline__ void fe_velocity_v(const F v[9], F rho, const F mn[9]
 // stencil) the equilibrium is the plain one with uu -> X plus p_g: its moments gain
 // e += rho A tr S + 6 p_g, zeta -= rho A tr S + 9 p_g, p_xx += rho A (S_xx - S_yy) / 3,
 // p_xy += rho A S_xy / 3.  COMP: the rest increment goes to *d0, v[0] unchanged.
+// Velocity derivatives of Eq. (24) at the cell from u_x (un) and u_y (wn) at x + c_i.
+template <class F>
+struct Strain {
+    F dxux, dyux, dxuy, dyuy;
+};
+template <class F>
+__device__ __forceinline__ Strain<F> strain_v(const F un[9], const F wn[9]) {
+    const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
+    Strain<F> g;
+    g.dxux = fmav(un[1] - un[3], w1, ((un[5] - un[7]) + (un[8] - un[6])) * w2);
+    g.dyux = fmav(un[2] - un[4], w1, ((un[5] - un[7]) + (un[6] - un[8])) * w2);
+    g.dxuy = fmav(wn[1] - wn[3], w1, ((wn[5] - wn[7]) + (wn[8] - wn[6])) * w2);
+    g.dyuy = fmav(wn[2] - wn[4], w1, ((wn[5] - wn[7]) + (wn[6] - wn[8])) * w2);
+    return g;
+}
+
+// st: the velocity derivatives of strain_v (taken before the populations are pulled, so that
+// the neighbours' velocities are no longer live during the collision).
 template <class F, bool COMP = false>
-__device__ __forceinline__ void fe_collide_iwb_v(F v[9], F rho, const F mn[9], const F rn[9], const F un[9],
-                                                 const F wn[9], F fx, F fy, F pg, float dpg, float A,
+__device__ __forceinline__ void fe_collide_iwb_v(F v[9], F rho, const F mn[9], const F rn[9], const Strain<F>& st,
+                                                 F fx, F fy, F pg, float dpg, float A,
                                                  const StepParams<float>& P, F* d0 = nullptr) {
     const F w1 = F::c(1.0f / 3.0f), w2 = F::c(1.0f / 12.0f);
     const F gmx = fmav(mn[1] - mn[3], w1, ((mn[5] - mn[7]) + (mn[8] - mn[6])) * w2);
@@ -64,10 +82,7 @@ __device__ __forceinline__ void fe_collide_iwb_v(F v[9], F rho, const F mn[9], c
     const F ux = fmav(F::c(0.5f), Fx, jx) * inv_rho;
     const F uy = fmav(F::c(0.5f), Fy, jy) * inv_rho;
     // strain rate from the velocity stencil (Eq. 24)
-    const F dxux = fmav(un[1] - un[3], w1, ((un[5] - un[7]) + (un[8] - un[6])) * w2);
-    const F dyux = fmav(un[2] - un[4], w1, ((un[5] - un[7]) + (un[6] - un[8])) * w2);
-    const F dxuy = fmav(wn[1] - wn[3], w1, ((wn[5] - wn[7]) + (wn[8] - wn[6])) * w2);
-    const F dyuy = fmav(wn[2] - wn[4], w1, ((wn[5] - wn[7]) + (wn[6] - wn[8])) * w2);
+    const F dxux = st.dxux, dyux = st.dyux, dxuy = st.dxuy, dyuy = st.dyuy;
     const F rA = rho * F::c(A);
     const F trS = F::c(2.0f) * (dxux + dyuy);
     const F rA3 = rA * F::c(1.0f / 3.0f);
@@ -160,7 +175,7 @@ __device__ __forceinline__ bool iwb_ring_produce(const float* __restrict__ fin, 
 
 // E.rho_g must be 0 (checked on the host): the buoyancy is -rho g and p_g vanishes.
 template <int NW, int S>
-__global__ void __launch_bounds__((NW + 1) * 32, 1) fe_iwb_pair(const float* __restrict__ fin,
+__global__ void __launch_bounds__((NW + 1) * 32, 3) fe_iwb_pair(const float* __restrict__ fin,
                                                                 float* __restrict__ fout, const StepParams<float> P,
                                                                 const Ext<float> E, int* __restrict__ err) {
     static_assert(S >= 6, "a consumer warp reads staged rows q-4 .. q+1 in one iteration");
@@ -261,14 +276,19 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) fe_iwb_pair(const float* __r
         }
         // collide row q-3 (ring indices k-5 .. k-3 hold source rows q-4 .. q-2)
         if (out && q >= y0 + 3) {
-            F2 v[9], mn[9], rn[9], un[9], wn[9];
+            Strain<F2> st;
+            {
+                F2 un[9], wn[9];
+                neighbours_pair(ux4, ux3, ux2, un);
+                neighbours_pair(uy4, uy3, uy2, wn);
+                st = strain_v(un, wn);
+            }
+            F2 v[9], mn[9], rn[9];
             pull_pair<WH>(sm.stage[(k - 5) % S], sm.stage[(k - 4) % S], sm.stage[(k - 3) % S], sc, v);
             neighbours_pair(m4, m3, m2, mn);
             neighbours_pair(r4, r3, r2, rn);
-            neighbours_pair(ux4, ux3, ux2, un);
-            neighbours_pair(uy4, uy3, uy2, wn);
             F2 d0;
-            fe_collide_iwb_v<F2, true>(v, r3.c, mn, rn, un, wn, fx, fy_of(r3.c), F2::c(0.0f), 0.0f, E.A, P, &d0);
+            fe_collide_iwb_v<F2, true>(v, r3.c, mn, rn, st, fx, fy_of(r3.c), F2::c(0.0f), 0.0f, E.A, P, &d0);
             cp_async_wait<3>();  // the copy of row q-3's extensions (three groups ago) has landed
             const unsigned ql3 = sm.qext[(q - 3 - y0 + 4) & 3][warp][lane];
             const unsigned qw = rest_update_pair(v[0], ql3, d0, P);  // compensated rest population
