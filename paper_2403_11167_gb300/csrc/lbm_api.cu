@@ -58,7 +58,10 @@ constexpr int kPPPStages = LBM_PPP_STAGES;
 static_assert(kPPPStages >= 4, "the pseudopotential strip ring needs at least 4 stages");
 using PPPSmem = lbmk::WarpStripSmem<kPPPWarps, kPPPStages, 60>;
 constexpr int kPPPTX = PPPSmem::TX;
-constexpr int kFEPWarps = 4;                   // consumer warps per CTA
+#ifndef LBM_FEP_WARPS
+#define LBM_FEP_WARPS 4
+#endif
+constexpr int kFEPWarps = LBM_FEP_WARPS;       // consumer warps per CTA
 constexpr int kFEPStages = LBM_FEP_STAGES;
 static_assert(kFEPStages >= 5, "the free-energy strip ring needs at least 5 stages");
 using FEPSmem = lbmk::WarpStripSmem<kFEPWarps, kFEPStages, 60>;
@@ -316,10 +319,11 @@ static size_t buffer_bytes(int precision, int nx, int ny) {
 }
 
 // Slots of the driven FP32 strip steps' per-warp stored mass: one per consumer warp of every
-// strip CTA (strip widths of at most 240 columns, strips of at least one row).
+// strip CTA of either model's strip kernel (strips of at least one row).
 static size_t drive_mass_slots(int nx, int ny) {
-    static_assert(kPPPTX == kFEPTX && kPPPWarps == kFEPWarps, "both strip kernels share one slot layout");
-    return (size_t)((nx + kPPPTX - 1) / kPPPTX) * (size_t)ny * kPPPWarps;
+    const size_t pp = (size_t)((nx + kPPPTX - 1) / kPPPTX) * kPPPWarps;
+    const size_t fe = (size_t)((nx + kFEPTX - 1) / kFEPTX) * kFEPWarps;
+    return std::max(pp, fe) * (size_t)ny;
 }
 
 extern "C" size_t lbm_workspace_bytes(int precision, int nx, int ny) {
@@ -573,9 +577,9 @@ static const real* launch_wall_solve(lbm_ctx* c, int src, const lbmk::StepParams
 
 // The drive of a state whose mass the previous driven strip step left in c->dmass (its
 // per-warp sums of the populations it stored): rho_ave = their fixed-order sum / cells.
-static lbmk::Drive<float> chained_drive(lbm_ctx* c, dim3 grid) {
+static lbmk::Drive<float> chained_drive(lbm_ctx* c, dim3 grid, int nwarps) {
     const long long n = (long long)c->nx * c->ny;
-    lbmk::mass_final_kernel<<<1, 32, 0, c->stream>>>(c->dmass, (int)(grid.x * grid.y) * kPPPWarps, 1.0 / (double)n,
+    lbmk::mass_final_kernel<<<1, 32, 0, c->stream>>>(c->dmass, (int)(grid.x * grid.y) * nwarps, 1.0 / (double)n,
                                                      c->partials + kMassBlocks);
     lbmk::Drive<float> d;
     d.rho_ave = c->partials + kMassBlocks;
@@ -595,8 +599,10 @@ static int launch_step_driven(lbm_ctx* c, int src, bool chained) {
     void* fout = c->f[src ^ 1];
     const bool pp = c->prm.model == LBM_PSEUDOPOTENTIAL;
     if (c->prec == LBM_F32 && c->use_tma) {
-        dim3 grid((c->nx + kPPPTX - 1) / kPPPTX, (c->ny + c->rows - 1) / c->rows);
-        const lbmk::Drive<float> d = chained ? chained_drive(c, grid) : launch_drive<float>(c, src);
+        const int tx = pp ? kPPPTX : kFEPTX;
+        dim3 grid((c->nx + tx - 1) / tx, (c->ny + c->rows - 1) / c->rows);
+        const lbmk::Drive<float> d =
+            chained ? chained_drive(c, grid, pp ? kPPPWarps : kFEPWarps) : launch_drive<float>(c, src);
         if (pp)
             lbmk::pp_step_pair<kPPPWarps, kPPPStages, true>
                 <<<grid, (kPPPWarps + 1) * 32, sizeof(PPPSmem), c->stream>>>((const float*)fin, (float*)fout, c->spf,
